@@ -1,0 +1,156 @@
+"""CPU oracle for the triplet merge tree (TEST INFRASTRUCTURE ONLY).
+
+The oracle is the plain, slow, sequential construction of Section 2.1 of the
+paper (sort the vertices, sweep them with union-find), written in C in
+``mt_oracle.c`` and loaded here with ctypes. It shares no code with the CUDA
+library. Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline /
+reference legs of ``bench.py`` may import this package; the library itself
+never does.
+
+Functions
+  merge_tree(f)            -> W   (uint64[n], W[u] = (s << 32) | v)
+  sort_order(f), sweep(f, order) the two phases of merge_tree, for timing
+  pairs(W)                 -> (pairs uint32[k, 2] = (minimum, saddle), roots)
+  components(f, t)         -> labels (uint32[n]; 0xFFFFFFFF outside G_t)
+  point_triplet(f, u, budget) -> W[u] or None if the query exceeds budget
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mt_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "ok", -1: "invalid", -2: "too large", -3: "non-finite", -4: "capacity", -6: "out of memory"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__(f"oracle status {code} ({STATUS.get(code, '?')})")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile mt_oracle.c into oracle/_build/liboracle.so (plain C, -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+    if stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            U32, U64 = ctypes.c_uint32, ctypes.c_uint64
+            for name, args in {
+                "oracle_sort_order": [P, U32, U32, U32, P],
+                "oracle_sweep": [P, U32, U32, U32, P, P],
+                "oracle_merge_tree": [P, U32, U32, U32, P],
+                "oracle_pairs": [P, U64, P, U64, P, P, P],
+                "oracle_components": [P, U32, U32, U32, ctypes.c_float, P],
+                "oracle_point_triplet": [P, U32, U32, U32, U64, U64, P],
+            }.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _field(f):
+    f = np.ascontiguousarray(np.asarray(f, dtype=np.float32))
+    if f.ndim == 1:
+        f = f.reshape(1, 1, -1)
+    if f.ndim == 2:
+        f = f.reshape(1, *f.shape)
+    if f.ndim != 3:
+        raise ValueError("field must be (nz, ny, nx)")
+    nz, ny, nx = f.shape
+    return f, nx, ny, nz
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(code: int):
+    if code != 0:
+        raise OracleError(code)
+
+
+def sort_order(f) -> np.ndarray:
+    f, nx, ny, nz = _field(f)
+    order = np.empty(f.size, dtype=np.uint32)
+    _check(_load().oracle_sort_order(_ptr(f), nx, ny, nz, _ptr(order)))
+    return order
+
+
+def sweep(f, order: np.ndarray) -> np.ndarray:
+    f, nx, ny, nz = _field(f)
+    order = np.ascontiguousarray(order, dtype=np.uint32)
+    W = np.empty(f.size, dtype=np.uint64)
+    _check(_load().oracle_sweep(_ptr(f), nx, ny, nz, _ptr(order), _ptr(W)))
+    return W
+
+
+def merge_tree(f) -> np.ndarray:
+    """Triplet merge tree W[u] = (s << 32) | v of the sublevel sets of f."""
+    f, nx, ny, nz = _field(f)
+    W = np.empty(f.size, dtype=np.uint64)
+    _check(_load().oracle_merge_tree(_ptr(f), nx, ny, nz, _ptr(W)))
+    return W
+
+
+def pairs(W: np.ndarray):
+    """(pairs[k, 2] = (minimum u, saddle s) by ascending u, roots list)."""
+    W = np.ascontiguousarray(W, dtype=np.uint64).ravel()
+    n = W.size
+    s = (W >> np.uint64(32)).astype(np.uint64)
+    cap = int(np.count_nonzero(s != np.arange(n, dtype=np.uint64)))
+    out = np.empty((max(cap, 1), 2), dtype=np.uint32)
+    npairs = ctypes.c_uint64(0)
+    nroots = ctypes.c_uint64(0)
+    root = ctypes.c_uint32(0xFFFFFFFF)
+    _check(_load().oracle_pairs(_ptr(W), n, _ptr(out), cap, ctypes.byref(npairs), ctypes.byref(nroots),
+                                ctypes.byref(root)))
+    k = int(npairs.value)
+    v = W & np.uint64(0xFFFFFFFF)
+    roots = np.nonzero((s == np.arange(n, dtype=np.uint64)) & (v == np.arange(n, dtype=np.uint64)))[0]
+    assert len(roots) == int(nroots.value)
+    return out[:k].copy(), roots.astype(np.uint32)
+
+
+def components(f, t: float) -> np.ndarray:
+    """Labels of the components of G_t = {f <= t}: the deepest vertex of each
+    component, 0xFFFFFFFF outside G_t. Built from f alone (no merge tree)."""
+    f, nx, ny, nz = _field(f)
+    lab = np.empty(f.size, dtype=np.uint32)
+    _check(_load().oracle_components(_ptr(f), nx, ny, nz, ctypes.c_float(t), _ptr(lab)))
+    return lab
+
+
+def point_triplet(f, u: int, budget: int = 1 << 20):
+    """W[u] computed for the single vertex u from the definitions, or None if
+    the query would visit more than ``budget`` vertices."""
+    f, nx, ny, nz = _field(f)
+    out = ctypes.c_uint64(0)
+    r = _load().oracle_point_triplet(_ptr(f), nx, ny, nz, int(u), int(budget), ctypes.byref(out))
+    if r < 0:
+        raise OracleError(r)
+    return int(out.value) if r == 1 else None
