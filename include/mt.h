@@ -1,0 +1,126 @@
+/*
+ * libmt -- triplet merge trees of scalar fields on regular grids, on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The method is the triplet merge tree of Smirnov and Morozov as adapted to
+ * GPUs in "Fast Merge Tree Computation via SYCL" (Nigmetov, Morozov,
+ * arXiv 2301.10838): Section 2.1 defines the merge tree, the triplet
+ * representation and the algorithms (Algorithms 1-5); Section 3.2 packs the
+ * pair (s, v) of each triplet into one 64-bit word so that a single-word
+ * compare-and-swap updates it.
+ *
+ * Conventions shared by every call
+ *   grid      nx * ny * nz vertices, x fastest: vertex (x, y, z) has linear
+ *             index u = x + nx * (y + ny * z); arrays are C order [nz][ny][nx].
+ *             1 <= n = nx*ny*nz < 2^32 - 1 (vertex ids are 32-bit, Section 3.2).
+ *   edges     6-neighbourhood: (x+-1, y, z), (x, y+-1, z), (x, y, z+-1).
+ *   order     a < b  <=>  f[a] < f[b]  or  (f[a] == f[b] and a < b), IEEE
+ *             comparison (-0 == +0). The paper assumes distinct values
+ *             (Section 2.1); the linear index breaks ties.
+ *   triplet   W[u] = ((uint64_t)s << 32) | v encodes the triplet (u, s, v) of
+ *             Section 2.1 in the 64-bit packing of Section 3.2:
+ *               s == v == u   u is the deepest vertex of its grid (root);
+ *               s == u != v   u lies inside a branch; v is the deepest vertex
+ *                             of u's component of the sublevel set at f(u);
+ *               s != u        u is a minimum whose branch merges at saddle s
+ *                             into the branch of v, v the deepest vertex of
+ *                             the component at level f(s).
+ *             The result is normalised and minimal (Section 2.1), hence unique:
+ *             it does not depend on launch shapes, timing or call mode.
+ *   memory    every pointer named d_* is device memory owned by the caller;
+ *             h_* is host memory. libmt never frees caller memory and keeps
+ *             no pointer after a call returns (the server below owns its own).
+ *   streams   `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *             Calls enqueue work on it and return without waiting unless
+ *             the description says they synchronise.
+ *   errors    argument errors are returned at once and enqueue nothing.
+ *             Errors found on the device (a non-finite value, a bounded loop
+ *             that hit its limit, a full output buffer) are recorded in a
+ *             status word inside the workspace and returned by the next call
+ *             that synchronises (mt_persistence_pairs, mt_sync_status).
+ *             A call that finds the status word already set does no work.
+ */
+#ifndef MT_H
+#define MT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    uint32_t nx, ny, nz;
+} mt_grid;
+
+typedef int32_t mt_status;
+#define MT_OK 0
+#define MT_ERR_INVALID (-1)   /* null pointer, zero side, misaligned or short buffer */
+#define MT_ERR_TOO_LARGE (-2) /* n >= 2^32 - 1 */
+#define MT_ERR_NONFINITE (-3) /* the field holds NaN or +-inf */
+#define MT_ERR_CAPACITY (-4)  /* an output buffer was too small; true count reported */
+#define MT_ERR_CUDA (-5)      /* a CUDA runtime call failed */
+#define MT_ERR_NOMEM (-6)     /* a device allocation failed (server only) */
+#define MT_ERR_TIMEOUT (-7)   /* a bounded device loop hit its iteration limit */
+#define MT_ERR_BUSY (-8)      /* server: the ticket is not finished yet */
+
+/* Human-readable name of a status code (static storage). */
+const char *mt_status_str(mt_status st);
+
+/* Bytes of device workspace that mt_build_triplets, mt_persistence_pairs and
+ * mt_components_at need for grid g (0 if g is invalid). The workspace must be
+ * 256-byte aligned; its contents need no initialisation and may be reused
+ * from call to call on the same stream. */
+size_t mt_workspace_bytes(mt_grid g);
+
+/*
+ * Triplet merge tree of the sublevel sets of f (Section 2.1, Algorithm 1).
+ *   d_f   float32[n], the field, C order [nz][ny][nx]; read only.
+ *   d_W   uint64[n], output triplets (layout above); 8-byte aligned.
+ *   d_ws  workspace of at least mt_workspace_bytes(g) bytes.
+ * Steps, all on the device: validate the values and seed every vertex with
+ * its lowest lower neighbour (the initialisation loop of Algorithm 1, seeded
+ * along steepest descent), merge every remaining grid edge with 64-bit
+ * compare-and-swap (Algorithms 2 and 3), and restore minimality by following
+ * representatives (Algorithms 4 and 5). Asynchronous; device-side errors
+ * (MT_ERR_NONFINITE, MT_ERR_TIMEOUT) land in the workspace status word.
+ */
+mt_status mt_build_triplets(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * 0-dimensional persistence pairs of the tree in d_W (Section 1: one point
+ * (f(a), f(b)) per branch, a a minimum and b the saddle where it merges).
+ *   d_pairs   uint32[cap][2]: (minimum u, saddle s) for every u with
+ *             W[u].s != u, by ascending u.
+ *   h_npairs  host; receives the true number of pairs.
+ *   h_root    host; receives the root vertex (W[u] = (u, u)); may be NULL.
+ * Synchronises `stream`. Returns the workspace status word if it is set,
+ * else MT_ERR_CAPACITY (first cap pairs written, true count in *h_npairs)
+ * if the pairs do not fit, else MT_OK. The number of pairs is the number of
+ * local minima minus one.
+ */
+mt_status mt_persistence_pairs(const float *d_f, const uint64_t *d_W, mt_grid g, uint32_t *d_pairs, uint64_t cap,
+                               uint64_t *h_npairs, uint32_t *h_root, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Connected components of the sublevel set G_t = {u : f[u] <= t}
+ * (Section 2.1), read off the tree: d_labels[u] is the representative of u
+ * at level t (Algorithm 4 with the value test f(s) <= t), i.e. the deepest
+ * vertex of u's component, or 0xFFFFFFFF when f[u] > t. Asynchronous.
+ *   d_labels  uint32[n], output.  t must not be NaN.
+ */
+mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t *d_labels,
+                           void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Synchronise `stream` and return (then clear) the workspace status word:
+ * MT_OK, MT_ERR_NONFINITE, MT_ERR_TIMEOUT or MT_ERR_CAPACITY.
+ */
+mt_status mt_sync_status(void *d_ws, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MT_H */

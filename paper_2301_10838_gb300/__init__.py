@@ -1,0 +1,35 @@
+"""Triplet merge trees of scalar fields on regular grids, native to GB300.
+
+The compute path is libmt (hand-written CUDA for sm_103a behind the C ABI of
+``include/mt.h``); ``binding`` is its thin ctypes binding with the same names.
+``fields`` holds the seeded synthetic inputs. Importing the package does not
+load libmt; the first ``mt_*`` call does, and raises if it is not built.
+"""
+
+from .binding import (  # noqa: F401
+    Grid,
+    MtError,
+    grid_of,
+    load,
+    mt_build_triplets,
+    mt_components_at,
+    mt_persistence_pairs,
+    mt_status_str,
+    mt_sync_status,
+    mt_workspace_bytes,
+    workspace,
+)
+
+__all__ = [
+    "Grid",
+    "MtError",
+    "grid_of",
+    "load",
+    "mt_build_triplets",
+    "mt_components_at",
+    "mt_persistence_pairs",
+    "mt_status_str",
+    "mt_sync_status",
+    "mt_workspace_bytes",
+    "workspace",
+]

@@ -1,0 +1,191 @@
+"""Thin ctypes binding of libmt (include/mt.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: it checks tensor placement, dtypes and sizes,
+passes raw device pointers and the current CUDA stream, and turns a non-OK
+status into ``MtError``. Every step of the path runs in libmt's kernels;
+there is no CPU fallback — if libmt.so is missing the call raises.
+
+Tensors: the field is float32 (nz, ny, nx) on a CUDA device; triplets are
+int64 (bit pattern of uint64 (s << 32) | v); pairs and labels are int32
+tensors holding uint32 bit patterns (view them with ``.view(torch.uint32)``
+or ``numpy().view(np.uint32)``).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "MtError",
+    "Grid",
+    "load",
+    "grid_of",
+    "mt_status_str",
+    "mt_workspace_bytes",
+    "mt_build_triplets",
+    "mt_persistence_pairs",
+    "mt_components_at",
+    "mt_sync_status",
+    "workspace",
+]
+
+MT_OK = 0
+STATUS_NAMES = {0: "MT_OK", -1: "MT_ERR_INVALID", -2: "MT_ERR_TOO_LARGE", -3: "MT_ERR_NONFINITE",
+                -4: "MT_ERR_CAPACITY", -5: "MT_ERR_CUDA", -6: "MT_ERR_NOMEM", -7: "MT_ERR_TIMEOUT",
+                -8: "MT_ERR_BUSY"}
+
+
+class MtError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = int(code)
+        name = STATUS_NAMES.get(self.code, str(code))
+        super().__init__(f"{where}: {name} ({mt_status_str(code)}){detail}")
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_uint32), ("ny", ctypes.c_uint32), ("nz", ctypes.c_uint32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+_SIGS = {
+    "mt_status_str": ([ctypes.c_int32], ctypes.c_char_p),
+    "mt_workspace_bytes": ([Grid], ctypes.c_size_t),
+    "mt_build_triplets": ([_P, Grid, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
+    "mt_persistence_pairs": ([_P, _P, Grid, _P, _U64, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
+    "mt_components_at": ([_P, _P, Grid, ctypes.c_float, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
+    "mt_sync_status": ([_P, _P], ctypes.c_int32),
+}
+
+
+def load() -> ctypes.CDLL:
+    """Load libmt.so (built in-tree by ``paper_2301_10838_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise ImportError(f"libmt.so is not built ({_build.LIB}); run "
+                                  "`python -m paper_2301_10838_gb300.build` on a machine with nvcc")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def mt_status_str(code: int) -> str:
+    try:
+        return load().mt_status_str(int(code)).decode()
+    except ImportError:
+        return STATUS_NAMES.get(int(code), "?")
+
+
+def grid_of(f: torch.Tensor) -> Grid:
+    if f.dim() != 3:
+        raise ValueError("field must be 3-D (nz, ny, nx)")
+    nz, ny, nx = (int(s) for s in f.shape)
+    return Grid(nx, ny, nz)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtypes, numel=None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name} must have dtype in {dtypes}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} needs at least {numel} elements, has {t.numel()}")
+    return t.data_ptr()
+
+
+def _check(code: int, where: str, detail: str = ""):
+    if code != MT_OK:
+        raise MtError(code, where, detail)
+
+
+_I64 = (torch.int64, getattr(torch, "uint64", torch.int64))
+_I32 = (torch.int32, getattr(torch, "uint32", torch.int32))
+
+
+def mt_workspace_bytes(grid: Grid) -> int:
+    return int(load().mt_workspace_bytes(grid))
+
+
+def workspace(grid: Grid, device=None) -> torch.Tensor:
+    """A device byte tensor big enough for ``grid`` (torch allocations are
+    256-byte aligned)."""
+    nbytes = mt_workspace_bytes(grid)
+    if nbytes == 0:
+        raise MtError(-1, "mt_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def mt_build_triplets(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    g = grid_of(f)
+    n = f.numel()
+    pf = _dev(f, "f", (torch.float32,))
+    pW = _dev(W, "W", _I64, n)
+    pws = _dev(ws, "ws", (torch.uint8,))
+    _check(load().mt_build_triplets(pf, g, pW, pws, ws.numel(), _stream_ptr(stream)), "mt_build_triplets")
+
+
+def mt_persistence_pairs(f: torch.Tensor, W: torch.Tensor, pairs: torch.Tensor, ws: torch.Tensor,
+                         stream=None, allow_partial: bool = False) -> tuple[int, int]:
+    """Writes (minimum, saddle) rows into ``pairs`` (int32, shape (cap, 2));
+    returns (npairs, root). Synchronises the stream."""
+    g = grid_of(f)
+    n = f.numel()
+    pf = _dev(f, "f", (torch.float32,))
+    pW = _dev(W, "W", _I64, n)
+    pws = _dev(ws, "ws", (torch.uint8,))
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must have shape (cap, 2)")
+    cap = int(pairs.shape[0])
+    pp = _dev(pairs, "pairs", _I32) if cap else 0
+    npairs = ctypes.c_uint64(0)
+    root = ctypes.c_uint32(0xFFFFFFFF)
+    code = load().mt_persistence_pairs(pf, pW, g, pp, cap, ctypes.byref(npairs), ctypes.byref(root), pws,
+                                       ws.numel(), _stream_ptr(stream))
+    if code == -4 and allow_partial:
+        return int(npairs.value), int(root.value)
+    _check(code, "mt_persistence_pairs", f" npairs={npairs.value} cap={cap}")
+    return int(npairs.value), int(root.value)
+
+
+def mt_components_at(f: torch.Tensor, W: torch.Tensor, t: float, labels: torch.Tensor, ws: torch.Tensor,
+                     stream=None) -> None:
+    g = grid_of(f)
+    n = f.numel()
+    pf = _dev(f, "f", (torch.float32,))
+    pW = _dev(W, "W", _I64, n)
+    pl = _dev(labels, "labels", _I32, n)
+    pws = _dev(ws, "ws", (torch.uint8,))
+    _check(load().mt_components_at(pf, pW, g, float(t), pl, pws, ws.numel(), _stream_ptr(stream)),
+           "mt_components_at")
+
+
+def mt_sync_status(ws: torch.Tensor, stream=None) -> None:
+    _check(load().mt_sync_status(_dev(ws, "ws", (torch.uint8,)), _stream_ptr(stream)), "mt_sync_status")

@@ -1,0 +1,157 @@
+// The C ABI of libmt (declared in include/mt.h): argument checks, workspace
+// layout, status handling, and the launches of the device steps.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "../../include/mt.h"
+#include "mt_device.cuh"
+#include "mt_internal.h"
+
+namespace mt {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace layout (all offsets 256-byte aligned):
+//   [0, 256)     status word, round flag
+//   [256, 512)   meta: npairs, number of roots, root
+//   [512, ...)   per-chunk counts of the ordered compaction
+size_t workspace_bytes(uint64_t n)
+{
+    const uint64_t nchunks = (n + kCompactChunk - 1) / kCompactChunk;
+    return 512 + align256(nchunks * sizeof(uint32_t));
+}
+
+bool carve_workspace(void *base, size_t bytes, uint64_t n, Workspace &ws)
+{
+    if (!base || ((uintptr_t)base & 255) || bytes < workspace_bytes(n)) return false;
+    char *p = static_cast<char *>(base);
+    ws.status = reinterpret_cast<uint32_t *>(p);
+    ws.more = reinterpret_cast<uint32_t *>(p + 4);
+    ws.meta = reinterpret_cast<uint64_t *>(p + 256);
+    ws.counts = reinterpret_cast<uint32_t *>(p + 512);
+    ws.nchunks = (n + kCompactChunk - 1) / kCompactChunk;
+    return true;
+}
+
+int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    return sms;
+}
+
+// Checks a grid; returns MT_OK and n, or the error.
+static mt_status grid_n(mt_grid g, uint64_t &n)
+{
+    if (g.nx == 0 || g.ny == 0 || g.nz == 0) return MT_ERR_INVALID;
+    n = (uint64_t)g.nx * g.ny * g.nz;
+    if (n >= 0xFFFFFFFFull) return MT_ERR_TOO_LARGE;
+    return MT_OK;
+}
+
+mt_status status_from_bits(uint32_t bits)
+{
+    if (bits & ST_NONFINITE) return MT_ERR_NONFINITE;
+    if (bits & ST_TIMEOUT) return MT_ERR_TIMEOUT;
+    if (bits & ST_CAPACITY) return MT_ERR_CAPACITY;
+    return MT_OK;
+}
+
+}  // namespace mt
+
+using namespace mt;
+
+extern "C" {
+
+const char *mt_status_str(mt_status st)
+{
+    switch (st) {
+    case MT_OK: return "ok";
+    case MT_ERR_INVALID: return "invalid argument";
+    case MT_ERR_TOO_LARGE: return "grid too large (n >= 2^32 - 1)";
+    case MT_ERR_NONFINITE: return "field holds a non-finite value";
+    case MT_ERR_CAPACITY: return "output buffer too small";
+    case MT_ERR_CUDA: return "CUDA runtime error";
+    case MT_ERR_NOMEM: return "out of device memory";
+    case MT_ERR_TIMEOUT: return "bounded device loop hit its limit";
+    case MT_ERR_BUSY: return "not finished yet";
+    default: return "unknown status";
+    }
+}
+
+size_t mt_workspace_bytes(mt_grid g)
+{
+    uint64_t n;
+    if (grid_n(g, n) != MT_OK) return 0;
+    return workspace_bytes(n);
+}
+
+mt_status mt_build_triplets(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, void *stream)
+{
+    uint64_t n;
+    mt_status st = grid_n(g, n);
+    if (st != MT_OK) return st;
+    if (!d_f || !d_W || ((uintptr_t)d_f & 3) || ((uintptr_t)d_W & 7)) return MT_ERR_INVALID;
+    Workspace ws;
+    if (!carve_workspace(d_ws, ws_bytes, n, ws)) return MT_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws.status, 0, 256, s) != cudaSuccess) return MT_ERR_CUDA;
+    if (launch_build(d_f, d_W, g.nx, g.ny, g.nz, ws, s) != cudaSuccess) return MT_ERR_CUDA;
+    return MT_OK;
+}
+
+mt_status mt_persistence_pairs(const float *d_f, const uint64_t *d_W, mt_grid g, uint32_t *d_pairs, uint64_t cap,
+                               uint64_t *h_npairs, uint32_t *h_root, void *d_ws, size_t ws_bytes, void *stream)
+{
+    uint64_t n;
+    mt_status st = grid_n(g, n);
+    if (st != MT_OK) return st;
+    if (!d_f || !d_W || !h_npairs || ((uintptr_t)d_W & 7) || (cap && (!d_pairs || ((uintptr_t)d_pairs & 3))))
+        return MT_ERR_INVALID;
+    Workspace ws;
+    if (!carve_workspace(d_ws, ws_bytes, n, ws)) return MT_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (launch_pairs(d_W, n, d_pairs, cap, ws, s) != cudaSuccess) return MT_ERR_CUDA;
+    uint64_t meta[3] = {0, 0, 0};
+    uint32_t bits = 0;
+    if (cudaMemcpyAsync(meta, ws.meta, sizeof(meta), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MT_ERR_CUDA;
+    if (cudaMemcpyAsync(&bits, ws.status, sizeof(bits), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return MT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MT_ERR_CUDA;
+    if (bits) return status_from_bits(bits);
+    *h_npairs = meta[0];
+    if (h_root) *h_root = meta[1] == 1 ? (uint32_t)meta[2] : 0xFFFFFFFFu;
+    if (meta[1] != 1) return MT_ERR_INVALID;  // not a tree of a connected grid
+    return meta[0] > cap ? MT_ERR_CAPACITY : MT_OK;
+}
+
+mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t *d_labels,
+                           void *d_ws, size_t ws_bytes, void *stream)
+{
+    uint64_t n;
+    mt_status st = grid_n(g, n);
+    if (st != MT_OK) return st;
+    if (!d_f || !d_W || !d_labels || std::isnan(t) || ((uintptr_t)d_W & 7) || ((uintptr_t)d_labels & 3))
+        return MT_ERR_INVALID;
+    Workspace ws;
+    if (!carve_workspace(d_ws, ws_bytes, n, ws)) return MT_ERR_INVALID;
+    if (launch_labels(d_f, d_W, n, t, d_labels, ws, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return MT_ERR_CUDA;
+    return MT_OK;
+}
+
+mt_status mt_sync_status(void *d_ws, void *stream)
+{
+    if (!d_ws || ((uintptr_t)d_ws & 255)) return MT_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t bits = 0;
+    if (cudaMemcpyAsync(&bits, d_ws, sizeof(bits), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MT_ERR_CUDA;
+    if (bits && cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) != cudaSuccess) return MT_ERR_CUDA;
+    return status_from_bits(bits);
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Device-side building blocks of the triplet merge tree (sm_103a).
+//
+// Triplet word:  W[u] = (s << 32) | v  encodes the triplet (u, s, v)
+// (Section 2.1; one 64-bit word per vertex as in Section 3.2, so that a single
+// 64-bit compare-and-swap updates the pair).
+// Order:         a < b  <=>  f[a] < f[b] || (f[a] == f[b] && a < b).
+#pragma once
+#include <cstdint>
+
+namespace mt {
+
+// Status bits kept in the first word of the workspace.
+enum : uint32_t {
+    ST_NONFINITE = 1u,
+    ST_TIMEOUT = 2u,
+    ST_CAPACITY = 4u,
+};
+
+// Limits of the bounded device loops. A merge that needs more steps than this
+// gives up and raises ST_TIMEOUT instead of spinning.
+constexpr uint32_t kMergeStepLimit = 1u << 24;
+constexpr uint32_t kChaseLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t tri_s(uint64_t w) { return (uint32_t)(w >> 32); }
+__device__ __forceinline__ uint32_t tri_v(uint64_t w) { return (uint32_t)w; }
+__device__ __forceinline__ uint64_t tri_pack(uint32_t s, uint32_t v) { return ((uint64_t)s << 32) | v; }
+__device__ __forceinline__ bool tri_is_root(uint64_t w, uint32_t u) { return w == tri_pack(u, u); }
+
+// a before b in the total order (value, index)
+__device__ __forceinline__ bool before(float fa, uint32_t a, float fb, uint32_t b)
+{
+    return fa < fb || (fa == fb && a < b);
+}
+
+// Loads of triplet words that other threads may be updating concurrently:
+// relaxed, device scope, so that they are not served from a stale L1 line.
+__device__ __forceinline__ uint64_t ld_tri(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_tri(uint64_t *p, uint64_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t cas_tri(uint64_t *p, uint64_t expect, uint64_t want)
+{
+    return atomicCAS(reinterpret_cast<unsigned long long *>(p), (unsigned long long)expect,
+                     (unsigned long long)want);
+}
+
+__device__ __forceinline__ void raise_status(uint32_t *status, uint32_t bit) { atomicOr(status, bit); }
+
+// Follow the triplet links from x while the link's saddle is at or below
+// level S (vertex order), i.e. walk to the deepest vertex that the current
+// tree connects to x below S (the climbs of Algorithm 3). Returns the word
+// of the vertex where it stops and leaves that vertex in x. A root word
+// (x, x) always stops the walk (the paper's pseudocode has no guard for it).
+__device__ __forceinline__ uint64_t climb(const uint64_t *W, const float *f, uint32_t &x, uint32_t S, float fS,
+                                          uint32_t &steps)
+{
+    uint64_t T = ld_tri(W + x);
+    for (;;) {
+        const uint32_t s = tri_s(T), t = tri_v(T);
+        if (s == x && t == x) break;  // root
+        if (s != S && !before(__ldg(f + s), s, fS, S)) break;  // saddle above S
+        x = t;
+        T = ld_tri(W + x);
+        if (++steps > kMergeStepLimit) break;
+    }
+    return T;
+}
+
+// Algorithm 3 (Merge), lock-free: make a and b connected at level S in the
+// triplet forest, given that they are connected below S in the graph.
+//   1. climb a and b to their deepest vertices u, v below S;
+//   2. if they coincide the edge adds nothing;
+//   3. otherwise order them so that u comes first and swing v's link to
+//      (S, u) with one 64-bit CAS (Algorithm 2);
+//   4. the link that v held before, (sv, tv), is not lost: if v was not a
+//      root, continue by merging u and tv at level sv. (A displaced root
+//      carries no link, so the merge ends there.)
+//   5. if the CAS fails another thread moved v first: climb again.
+// Returns false if the step budget ran out.
+__device__ __forceinline__ bool merge(uint64_t *W, const float *f, uint32_t S, uint32_t a, uint32_t b)
+{
+    float fS = __ldg(f + S);
+    uint32_t u = a, v = b;
+    uint32_t steps = 0;
+    for (;;) {
+        uint64_t Tu = climb(W, f, u, S, fS, steps);
+        uint64_t Tv = climb(W, f, v, S, fS, steps);
+        if (++steps > kMergeStepLimit) return false;
+        if (u == v) return true;
+        if (before(__ldg(f + v), v, __ldg(f + u), u)) {
+            uint32_t tx = u;
+            u = v;
+            v = tx;
+            uint64_t tT = Tu;
+            Tu = Tv;
+            Tv = tT;
+        }
+        const uint64_t old = cas_tri(W + v, Tv, tri_pack(S, u));
+        if (old == Tv) {
+            const uint32_t sv = tri_s(Tv), tv = tri_v(Tv);
+            if (sv == v && tv == v) return true;  // displaced a root
+            S = sv;
+            fS = __ldg(f + sv);
+            v = tv;
+        }
+    }
+}
+
+// Representative (Algorithm 4) of x at level S given as a vertex: the deepest
+// vertex of x's component below S. Hops while the link's saddle s' satisfies
+// s' <= S in the vertex order and returns the vertex where it stops (the
+// printed algorithm returns one hop further; the vertex itself is the one
+// the definition asks for).
+__device__ __forceinline__ uint32_t representative(const uint64_t *W, const float *f, uint32_t x, uint32_t S, float fS,
+                                                   uint32_t &steps)
+{
+    for (;;) {
+        const uint64_t T = ld_tri(W + x);
+        const uint32_t s = tri_s(T), t = tri_v(T);
+        if (s == x && t == x) return x;
+        if (s != S && !before(__ldg(f + s), s, fS, S)) return x;
+        x = t;
+        if (++steps > kChaseLimit) return x;
+    }
+}
+
+}  // namespace mt

@@ -1,0 +1,178 @@
+// Queries on a finished triplet merge tree:
+//   k_pairs_count / k_scan_counts / k_pairs_write
+//       0-dimensional persistence pairs (minimum u, saddle s) for every u with
+//       W[u].s != u, in ascending u (ordered stream compaction);
+//   k_labels
+//       representatives at a threshold t (components of G_t).
+#include <cuda_runtime.h>
+
+#include "mt_device.cuh"
+#include "mt_internal.h"
+
+namespace mt {
+
+// ------------------------------------------------------------------ pairs
+//
+// One CTA per chunk of kCompactChunk consecutive vertices, read in 16 rounds
+// of 256 consecutive vertices so that every load is coalesced. A pass counts
+// the pairs of each chunk (and finds the roots), a single-CTA scan turns the
+// counts into offsets, and a second pass writes each chunk's pairs at its
+// offset in order. Each round ranks its flags with warp ballots plus a
+// prefix over the 8 warp totals, which keeps the ascending order.
+constexpr int kCompactThreads = 256;
+constexpr int kCompactRounds = kCompactChunk / kCompactThreads;
+
+__global__ void __launch_bounds__(kCompactThreads) k_pairs_count(const uint64_t *__restrict__ W, uint64_t n,
+                                                                 uint32_t *counts, uint64_t *meta,
+                                                                 const uint32_t *status)
+{
+    if (*status) return;
+    __shared__ uint32_t warp_sum[kCompactThreads / 32];
+    const uint64_t b0 = (uint64_t)blockIdx.x * kCompactChunk;
+    uint32_t c = 0;
+    for (int r = 0; r < kCompactRounds; r++) {
+        const uint64_t u = b0 + (uint64_t)r * kCompactThreads + threadIdx.x;
+        if (u >= n) break;
+        const uint64_t T = W[u];
+        if (tri_s(T) != (uint32_t)u) {
+            c++;
+        } else if (tri_v(T) == (uint32_t)u) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(meta + 1), 1ull);
+            meta[2] = u;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int w = 0; w < kCompactThreads / 32; w++) tot += warp_sum[w];
+        counts[blockIdx.x] = tot;
+    }
+}
+
+// Exclusive scan of counts[0..m) in place by one CTA of 1024 threads; the
+// total goes to meta[0].
+__global__ void __launch_bounds__(1024) k_scan_counts(uint32_t *counts, uint64_t m, uint64_t *meta,
+                                                      const uint32_t *status)
+{
+    if (*status) return;
+    __shared__ uint64_t part[1024];
+    const uint64_t per = (m + 1023) / 1024;
+    const uint64_t a = threadIdx.x * per, b = a + per < m ? a + per : m;
+    uint64_t s = 0;
+    for (uint64_t i = a; i < b; i++) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the 1024 partial sums
+    for (int o = 1; o < 1024; o <<= 1) {
+        const uint64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (uint64_t i = a; i < b; i++) {
+        const uint32_t c = counts[i];
+        counts[i] = (uint32_t)run;
+        run += c;
+    }
+    if (threadIdx.x == 1023) meta[0] = part[1023];
+}
+
+__global__ void __launch_bounds__(kCompactThreads) k_pairs_write(const uint64_t *__restrict__ W, uint64_t n,
+                                                                 const uint32_t *offsets, uint32_t *pairs,
+                                                                 uint64_t cap, const uint32_t *status)
+{
+    if (*status) return;
+    __shared__ uint32_t warp_cnt[kCompactThreads / 32];
+    const uint64_t b0 = (uint64_t)blockIdx.x * kCompactChunk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t run = offsets[blockIdx.x];
+    for (int r = 0; r < kCompactRounds; r++) {
+        const uint64_t u = b0 + (uint64_t)r * kCompactThreads + threadIdx.x;
+        if (b0 + (uint64_t)r * kCompactThreads >= n) break;  // uniform across the CTA
+        uint64_t T = 0;
+        bool flag = false;
+        if (u < n) {
+            T = W[u];
+            flag = tri_s(T) != (uint32_t)u;
+        }
+        const uint32_t ball = __ballot_sync(0xffffffffu, flag);
+        if (lane == 0) warp_cnt[warp] = __popc(ball);
+        __syncthreads();
+        uint32_t before_w = 0, total = 0;
+        for (int w = 0; w < kCompactThreads / 32; w++) {
+            const uint32_t c = warp_cnt[w];
+            before_w += w < warp ? c : 0;
+            total += c;
+        }
+        if (flag) {
+            const uint64_t pos = run + before_w + __popc(ball & ((1u << lane) - 1u));
+            if (pos < cap) {
+                pairs[2 * pos] = (uint32_t)u;
+                pairs[2 * pos + 1] = tri_s(T);
+            }
+        }
+        run += total;
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
+                         cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(ws.meta, 0, 3 * sizeof(uint64_t), st);
+    if (e != cudaSuccess) return e;
+    k_pairs_count<<<(unsigned)ws.nchunks, kCompactThreads, 0, st>>>(W, n, ws.counts, ws.meta, ws.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_scan_counts<<<1, 1024, 0, st>>>(ws.counts, ws.nchunks, ws.meta, ws.status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_pairs_write<<<(unsigned)ws.nchunks, kCompactThreads, 0, st>>>(W, n, ws.counts, pairs, cap, ws.status);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- labels
+//
+// Components of G_t = {u : f[u] <= t} (Section 2.1): the label of u is its
+// representative at level t (Algorithm 4 with the value test f(s) <= t that
+// the paper's Representative uses), the deepest vertex of u's component, or
+// 0xFFFFFFFF when f[u] > t. An inner vertex u with f[u] <= t hops to its
+// deepest vertex v first (its link's saddle is u itself), then the chain of
+// branch links is followed while their saddles lie in G_t.
+__global__ void __launch_bounds__(256) k_labels(const float *__restrict__ f, const uint64_t *__restrict__ W,
+                                                uint64_t n, float t, uint32_t *__restrict__ labels,
+                                                uint32_t *status)
+{
+    if (*status) return;
+    for (uint64_t uu = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; uu < n;
+         uu += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = (uint32_t)uu;
+        uint32_t lab = 0xFFFFFFFFu;
+        if (__ldg(f + u) <= t) {
+            uint32_t x = u;
+            for (uint32_t h = 0;; h++) {
+                const uint64_t T = __ldg(reinterpret_cast<const unsigned long long *>(W) + x);
+                const uint32_t s = tri_s(T);
+                if (T == tri_pack(x, x) || !(__ldg(f + s) <= t)) break;
+                x = tri_v(T);
+                if (h > kChaseLimit) {
+                    raise_status(status, ST_TIMEOUT);
+                    break;
+                }
+            }
+            lab = x;
+        }
+        labels[uu] = lab;
+    }
+}
+
+cudaError_t launch_labels(const float *f, const uint64_t *W, uint64_t n, float t, uint32_t *labels, Workspace &ws,
+                          cudaStream_t st)
+{
+    const uint64_t want = (n + 255) / 256, cap = (uint64_t)device_sms() * 8;
+    k_labels<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(f, W, n, t, labels, ws.status);
+    return cudaGetLastError();
+}
+
+}  // namespace mt

@@ -1,0 +1,95 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares
+(no compute calls: this runs without a GPU)."""
+
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2301_10838_gb300 as mt
+from paper_2301_10838_gb300 import binding
+from paper_2301_10838_gb300 import build as mtbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(mt_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    mtbuild.build()
+    return mt.load()
+
+
+def test_header_declares_the_path_entry_points():
+    names = _declared()
+    for need in ("mt_build_triplets", "mt_persistence_pairs", "mt_components_at", "mt_workspace_bytes"):
+        assert need in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", mtbuild.LIB], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = _declared() - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+    for name in _declared():
+        assert getattr(lib, name) is not None
+
+
+def test_binding_covers_the_header():
+    assert set(binding.exported_symbols()) <= _declared()
+
+
+def test_status_strings(lib):
+    for code in range(-8, 1):
+        s = mt.mt_status_str(code)
+        assert s and s != "unknown status"
+
+
+def test_workspace_query(lib):
+    assert mt.mt_workspace_bytes(mt.Grid(0, 4, 4)) == 0
+    assert mt.mt_workspace_bytes(mt.Grid(65536, 65536, 1)) == 0  # n = 2^32: too large
+    a = mt.mt_workspace_bytes(mt.Grid(64, 64, 64))
+    b = mt.mt_workspace_bytes(mt.Grid(1024, 1024, 1024))
+    assert 0 < a <= b
+    assert a % 256 == 0 and b % 256 == 0
+
+
+def test_argument_errors_need_no_gpu(lib):
+    """Argument checks return before touching the device."""
+    g = mt.Grid(4, 4, 4)
+    nbytes = lib.mt_workspace_bytes(g)
+    assert lib.mt_build_triplets(None, g, None, None, nbytes, None) == -1
+    assert lib.mt_build_triplets(ctypes.c_void_p(256), mt.Grid(0, 1, 1), ctypes.c_void_p(256),
+                                 ctypes.c_void_p(256), nbytes, None) == -1
+    assert lib.mt_build_triplets(ctypes.c_void_p(256), mt.Grid(65536, 65536, 1), ctypes.c_void_p(256),
+                                 ctypes.c_void_p(256), nbytes, None) == -2
+    # misaligned workspace / short workspace
+    assert lib.mt_build_triplets(ctypes.c_void_p(256), g, ctypes.c_void_p(256), ctypes.c_void_p(260),
+                                 nbytes, None) == -1
+    assert lib.mt_build_triplets(ctypes.c_void_p(256), g, ctypes.c_void_p(256), ctypes.c_void_p(256),
+                                 nbytes - 1, None) == -1
+    assert lib.mt_components_at(ctypes.c_void_p(256), ctypes.c_void_p(256), g, float("nan"),
+                                ctypes.c_void_p(256), ctypes.c_void_p(256), nbytes, None) == -1
+    npairs = ctypes.c_uint64(0)
+    assert lib.mt_persistence_pairs(ctypes.c_void_p(256), ctypes.c_void_p(256), g, None, 0, None, None,
+                                    ctypes.c_void_p(256), nbytes, None) == -1
+
+
+def test_library_is_sm103a_only():
+    """The build passes exactly one -gencode, for sm_103a."""
+    assert mtbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
