@@ -119,6 +119,25 @@ mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, flo
  */
 mt_status mt_sync_status(void *d_ws, void *stream);
 
+/* ------------------------------------------------------------- tracing
+ * Not part of the paper's method: diagnostics for benchmarks and profiling.
+ * When enabled, every step (init, descend, merge, repair, pairs, labels, ...)
+ * is bracketed by CUDA events on the stream it runs on; mt_trace_read waits
+ * for the recorded events and returns the accumulated device time per step.
+ */
+typedef struct {
+    char name[16];
+    unsigned long long calls;
+    double total_ms;
+} mt_phase_time;
+
+void mt_trace_enable(int on);
+/* Fills up to max_entries rows (steps with at least one call), returns how
+ * many steps have data; reset != 0 clears the totals afterwards. */
+int mt_trace_read(mt_phase_time *out, int max_entries, int reset);
+/* Number of kernels libmt has launched in this process so far. */
+unsigned long long mt_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,10 @@ from .binding import (  # noqa: F401
     mt_components_at,
     mt_persistence_pairs,
     mt_status_str,
+    mt_kernel_launches,
     mt_sync_status,
+    mt_trace_enable,
+    mt_trace_read,
     mt_workspace_bytes,
     workspace,
 )
@@ -30,6 +33,9 @@ __all__ = [
     "mt_persistence_pairs",
     "mt_status_str",
     "mt_sync_status",
+    "mt_trace_enable",
+    "mt_trace_read",
+    "mt_kernel_launches",
     "mt_workspace_bytes",
     "workspace",
 ]

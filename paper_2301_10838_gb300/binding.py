@@ -33,6 +33,9 @@ __all__ = [
     "mt_persistence_pairs",
     "mt_components_at",
     "mt_sync_status",
+    "mt_trace_enable",
+    "mt_trace_read",
+    "mt_kernel_launches",
     "workspace",
 ]
 
@@ -65,6 +68,9 @@ _SIGS = {
     "mt_persistence_pairs": ([_P, _P, Grid, _P, _U64, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_components_at": ([_P, _P, Grid, ctypes.c_float, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_sync_status": ([_P, _P], ctypes.c_int32),
+    "mt_trace_enable": ([ctypes.c_int], None),
+    "mt_trace_read": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "mt_kernel_launches": ([], ctypes.c_ulonglong),
 }
 
 
@@ -189,3 +195,22 @@ def mt_components_at(f: torch.Tensor, W: torch.Tensor, t: float, labels: torch.T
 
 def mt_sync_status(ws: torch.Tensor, stream=None) -> None:
     _check(load().mt_sync_status(_dev(ws, "ws", (torch.uint8,)), _stream_ptr(stream)), "mt_sync_status")
+
+
+class PhaseTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 16), ("calls", ctypes.c_ulonglong), ("total_ms", ctypes.c_double)]
+
+
+def mt_trace_enable(on: bool = True) -> None:
+    load().mt_trace_enable(1 if on else 0)
+
+
+def mt_trace_read(reset: bool = True) -> dict[str, tuple[int, float]]:
+    """{step name: (calls, total device ms)} accumulated since the last reset."""
+    rows = (PhaseTime * 16)()
+    k = load().mt_trace_read(ctypes.cast(rows, ctypes.c_void_p), 16, 1 if reset else 0)
+    return {rows[i].name.decode(): (int(rows[i].calls), float(rows[i].total_ms)) for i in range(min(k, 16))}
+
+
+def mt_kernel_launches() -> int:
+    return int(load().mt_kernel_launches())

@@ -223,29 +223,42 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
     const bool vec = (nx % 4 == 0) && ((uintptr_t)f % 16 == 0) && ((uintptr_t)W % 16 == 0);
     const uint32_t nxq = vec ? nx / 4 : nx;
     const uint32_t nthreads = nxq * ny * nz;
-    if (vec)
-        k_init<4><<<grid_for(nthreads, 256), 256, 0, st>>>(f, W, nx, ny, nz, nxq, nthreads, ws.status);
-    else
-        k_init<1><<<grid_for(nthreads, 256), 256, 0, st>>>(f, W, nx, ny, nz, nxq, nthreads, ws.status);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // descent rounds: at most ~log_{hops}(n) + 2 of them
-    for (int round = 0; round < 40; round++) {
-        e = cudaMemsetAsync(ws.more, 0, sizeof(uint32_t), st);
-        if (e != cudaSuccess) return e;
-        k_descend<<<grid_for(n, 256), 256, 0, st>>>(W, n, 64, ws.more, ws.status);
+    cudaError_t e;
+    {
+        PhaseScope ps(kInit, st);
+        if (vec)
+            k_init<4><<<grid_for(nthreads, 256), 256, 0, st>>>(f, W, nx, ny, nz, nxq, nthreads, ws.status);
+        else
+            k_init<1><<<grid_for(nthreads, 256), 256, 0, st>>>(f, W, nx, ny, nz, nxq, nthreads, ws.status);
+        count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        uint32_t more = 0;
-        e = cudaMemcpyAsync(&more, ws.more, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return e;
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-        if (!more) break;
     }
-    k_merge<<<grid_for(n, 256), 256, 0, st>>>(W, f, nx, ny, nz, n, ws.status);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    {
+        // descent rounds: at most ~log_{hops}(n) + 2 of them
+        PhaseScope ps(kDescend, st);
+        for (int round = 0; round < 40; round++) {
+            if ((e = cudaMemsetAsync(ws.more, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+            k_descend<<<grid_for(n, 256), 256, 0, st>>>(W, n, 64, ws.more, ws.status);
+            count_launch();
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            uint32_t more = 0;
+            if ((e = cudaMemcpyAsync(&more, ws.more, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return e;
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+            if (!more) break;
+        }
+    }
+    {
+        PhaseScope ps(kMerge, st);
+        k_merge<<<grid_for(n, 256), 256, 0, st>>>(W, f, nx, ny, nz, n, ws.status);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    PhaseScope ps(kRepair, st);
     k_repair<<<grid_for(n, 256), 256, 0, st>>>(W, f, n, 0, ws.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_repair<<<grid_for(n, 256), 256, 0, st>>>(W, f, n, 1, ws.status);
+    count_launch(2);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,23 @@ struct Workspace {
     uint64_t nchunks;
 };
 
+// Tracing (mt_trace.cu): phases timed with events on the launching stream.
+enum Phase { kInit = 0, kDescend, kMerge, kRepair, kPairs, kLabels, kBatch, kTile, kPhaseCount };
+const char *phase_name(int p);
+void count_launch(unsigned k = 1);
+class PhaseScope {
+  public:
+    PhaseScope(int phase, cudaStream_t st);
+    ~PhaseScope();
+    PhaseScope(const PhaseScope &) = delete;
+    PhaseScope &operator=(const PhaseScope &) = delete;
+
+  private:
+    int phase_;
+    cudaStream_t st_;
+    void *a_;
+};
+
 size_t workspace_bytes(uint64_t n);
 bool carve_workspace(void *base, size_t bytes, uint64_t n, Workspace &ws);
 int device_sms();

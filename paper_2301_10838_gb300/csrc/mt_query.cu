@@ -122,8 +122,10 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(const uint64_t 
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
                          cudaStream_t st)
 {
+    PhaseScope ps(kPairs, st);
     cudaError_t e = cudaMemsetAsync(ws.meta, 0, 3 * sizeof(uint64_t), st);
     if (e != cudaSuccess) return e;
+    count_launch(3);
     k_pairs_count<<<(unsigned)ws.nchunks, kCompactThreads, 0, st>>>(W, n, ws.counts, ws.meta, ws.status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_scan_counts<<<1, 1024, 0, st>>>(ws.counts, ws.nchunks, ws.meta, ws.status);
@@ -170,6 +172,8 @@ __global__ void __launch_bounds__(256) k_labels(const float *__restrict__ f, con
 cudaError_t launch_labels(const float *f, const uint64_t *W, uint64_t n, float t, uint32_t *labels, Workspace &ws,
                           cudaStream_t st)
 {
+    PhaseScope ps(kLabels, st);
+    count_launch();
     const uint64_t want = (n + 255) / 256, cap = (uint64_t)device_sms() * 8;
     k_labels<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(f, W, n, t, labels, ws.status);
     return cudaGetLastError();
