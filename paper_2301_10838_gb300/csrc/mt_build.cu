@@ -1,7 +1,8 @@
 // Kernels that build the triplet merge tree (Algorithm 1 of the paper):
-//   k_init     initialisation, seeded with the lowest lower neighbour
-//   k_descend  pointer jumping along the steepest-descent links
-//   k_merge    Merge (Algorithm 3) of every grid edge with 64-bit CAS
+//   k_tile     per tile, in shared memory: initialisation seeded with the
+//              lowest lower neighbour, descent pointer jumping, Merge of the
+//              in-tile edges, Repair
+//   k_cross    Merge (Algorithm 3) of the edges between tiles, 64-bit CAS
 //   k_repair   Repair (Algorithm 5) via Representative (Algorithm 4)
 #include <cuda_runtime.h>
 
@@ -10,171 +11,366 @@
 
 namespace mt {
 
-// ---------------------------------------------------------------- k_init
+// ---------------------------------------------------------------- k_tile
 //
-// Algorithm 1 starts from the tree of the graph without edges, T[u] = (u, u).
-// Here every vertex u that has a neighbour before it starts from
-// T[u] = (u, lln(u)) instead, lln(u) its lowest lower 6-neighbour: this is a
-// valid normalised triplet of the graph that holds only the steepest-descent
-// edges (lln(u) comes before u and the two are joined at level f(u)), so the
-// merge phase may start from it; the descent edge itself then needs no merge.
-// lln(u) is the first vertex of the closed neighbourhood {u} + N(u) in the
-// vertex order, and u is a local minimum iff that first vertex is u itself.
+// The initialisation loop and most of the edge loop of Algorithm 1, one
+// brick ("tile") of the grid per CTA, entirely in shared memory.
 //
-// Each thread handles V consecutive x of one row (V = 4 with float4 loads
-// when rows are 16-byte aligned). The stencil rows y+-1 and z+-1 are re-read
-// by the neighbouring rows' threads and served from L1/L2, so HBM sees each
-// value about once. Non-finite values raise ST_NONFINITE.
-template <int V>
-__global__ void __launch_bounds__(256) k_init(const float *__restrict__ f, uint64_t *__restrict__ W, uint32_t nx,
-                                              uint32_t ny, uint32_t nz, uint32_t nxq, uint32_t nthreads,
-                                              uint32_t *status)
+// Algorithm 1 may merge the edges in any order. This kernel merges first the
+// edges inside each tile: it loads the tile's values into shared memory
+// (coalesced float4 rows), builds the triplet tree of the tile's own subgraph
+// with the lock-free Merge (32-bit CAS on shared memory, local ids packed as
+// (s << 16) | v), repairs it, and writes it out as global triplets. Local ids
+// l = lx + TX * (ly + TY * lz) order the tile's vertices exactly as their
+// global linear indices do, so ties break identically. Values are kept as
+// 32-bit keys whose unsigned order is the float order (-0 and +0 share one
+// key), so a vertex comparison is an integer comparison of (key, id).
+//
+// Within the tile the initial tree is seeded along steepest descent:
+// T[l] = (l, lln(l)) with lln(l) the first vertex of l's closed in-tile
+// neighbourhood (a normalised triplet of the graph of descent edges); pointer
+// jumping then moves every inner vertex straight to the minimum its descent
+// reaches, and an edge whose two ends reach the same minimum needs no merge.
+//
+// The merges themselves are organised for SIMT execution: the CTA first
+// lists the edges that need a merge (task list in shared memory), then every
+// lane pulls tasks dynamically and advances its merge by one climb step per
+// iteration of a loop in which the whole warp stays converged, so lanes with
+// short and long climbs do not serialise each other.
+//
+// What leaves the kernel is, for every vertex, its triplet in the subgraph
+// induced by its tile: a valid normalised triplet tree of the full grid minus
+// the edges between tiles, which k_cross merges next.
+template <int LX, int LY, int LZ>
+struct Tile {
+    static constexpr int TX = 1 << LX, TY = 1 << LY, TZ = 1 << LZ;
+    static constexpr int TV = TX * TY * TZ;
+    static_assert(TV <= 16384, "tasks pack a local id and a direction into 16 bits");
+    static_assert(TX % 4 == 0, "rows are loaded as float4");
+    // shared memory: keys, triplets (4 B each) and up to 3 tasks (2 B each)
+    static constexpr size_t kSmem = (size_t)TV * (4 + 4 + 6);
+};
+
+__device__ __forceinline__ uint32_t sm_pack(uint32_t s, uint32_t v) { return (s << 16) | v; }
+__device__ __forceinline__ uint32_t sm_s(uint32_t w) { return w >> 16; }
+__device__ __forceinline__ uint32_t sm_v(uint32_t w) { return w & 0xFFFFu; }
+
+// Order-preserving 32-bit key of a float (+0 and -0 map to the same key).
+__device__ __forceinline__ uint32_t order_key(float x)
 {
+    const uint32_t b = x == 0.0f ? 0u : __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+// (ka, a) before (kb, b)
+__device__ __forceinline__ bool kbefore(uint32_t ka, uint32_t a, uint32_t kb, uint32_t b)
+{
+    return ka < kb || (ka == kb && a < b);
+}
+
+// Representative (Algorithm 4) in the tile's tree at level (kS, S).
+// Every link leads to an earlier vertex, so a chain is shorter than the tile;
+// a longer one can only come from a corrupted tree and clears ok.
+template <int TV>
+__device__ __forceinline__ uint32_t sm_rep(const uint32_t *T, const uint32_t *K, uint32_t x, uint32_t S,
+                                           uint32_t kS, bool &ok)
+{
+    const volatile uint32_t *vT = T;
+    for (uint32_t h = 0; h < (uint32_t)TV; h++) {
+        const uint32_t w = vT[x];
+        if (w == sm_pack(x, x)) return x;
+        const uint32_t s = sm_s(w);
+        if (s != S && !kbefore(K[s], s, kS, S)) return x;
+        x = sm_v(w);
+    }
+    ok = false;
+    return x;
+}
+
+template <int LX, int LY, int LZ, int NT>
+__global__ void __launch_bounds__(NT, 2) k_tile(const float *__restrict__ f, uint64_t *__restrict__ W, uint32_t nx,
+                                                uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty, int vec,
+                                                uint32_t *status)
+{
+    using TS = Tile<LX, LY, LZ>;
+    constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV;
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *K = smem;       // order keys
+    uint32_t *T = smem + TV;  // triplets (s << 16) | v
+    uint16_t *task = reinterpret_cast<uint16_t *>(smem + 2 * TV);
+    __shared__ uint32_t s_ntask, s_next;
+
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+    const uint32_t wx = min((uint32_t)TX, nx - x0), wy = min((uint32_t)TY, ny - y0),
+                   wz = min((uint32_t)TZ, nz - z0);
     const uint64_t nxy = (uint64_t)nx * ny;
-    for (uint64_t tt = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; tt < nthreads;
-         tt += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = (uint32_t)tt;
-        const uint32_t xq = t % nxq;
-        const uint32_t row = t / nxq;  // y + ny * z
-        const uint32_t y = row % ny, z = row / ny;
-        const uint32_t x0 = xq * V;
-        const uint64_t base = (uint64_t)row * nx + x0;
-        float c[V], ym[V], yp[V], zm[V], zp[V];
-        if constexpr (V == 4) {
-            const float4 cc = __ldg(reinterpret_cast<const float4 *>(f + base));
-            c[0] = cc.x, c[1] = cc.y, c[2] = cc.z, c[3] = cc.w;
-            if (y > 0) {
-                const float4 q = __ldg(reinterpret_cast<const float4 *>(f + base - nx));
-                ym[0] = q.x, ym[1] = q.y, ym[2] = q.z, ym[3] = q.w;
+    const uint64_t base = (uint64_t)z0 * nxy + (uint64_t)y0 * nx + x0;
+    auto lxo = [](uint32_t l) { return l & (TX - 1); };
+    auto lyo = [](uint32_t l) { return (l >> LX) & (TY - 1); };
+    auto lzo = [](uint32_t l) { return l >> (LX + LY); };
+    auto valid = [&](uint32_t l) { return lxo(l) < wx && lyo(l) < wy && lzo(l) < wz; };
+    auto gid = [&](uint32_t l) {
+        return (uint32_t)(base + (uint64_t)lzo(l) * nxy + (uint64_t)lyo(l) * nx + lxo(l));
+    };
+    if (threadIdx.x == 0) s_ntask = 0, s_next = 0;
+
+    // 1. load the tile's values (rows of TX floats) as order keys
+    bool bad = false;
+    if (vec) {
+        for (uint32_t q = threadIdx.x; q < TV / 4; q += NT) {
+            const uint32_t l = 4 * q;
+            if (lxo(l) < wx && lyo(l) < wy && lzo(l) < wz) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(f + gid(l)));
+                bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
+                *reinterpret_cast<uint4 *>(K + l) = make_uint4(order_key(v.x), order_key(v.y), order_key(v.z),
+                                                              order_key(v.w));
             }
-            if (y + 1 < ny) {
-                const float4 q = __ldg(reinterpret_cast<const float4 *>(f + base + nx));
-                yp[0] = q.x, yp[1] = q.y, yp[2] = q.z, yp[3] = q.w;
-            }
-            if (z > 0) {
-                const float4 q = __ldg(reinterpret_cast<const float4 *>(f + base - nxy));
-                zm[0] = q.x, zm[1] = q.y, zm[2] = q.z, zm[3] = q.w;
-            }
-            if (z + 1 < nz) {
-                const float4 q = __ldg(reinterpret_cast<const float4 *>(f + base + nxy));
-                zp[0] = q.x, zp[1] = q.y, zp[2] = q.z, zp[3] = q.w;
-            }
-        } else {
-            c[0] = __ldg(f + base);
-            if (y > 0) ym[0] = __ldg(f + base - nx);
-            if (y + 1 < ny) yp[0] = __ldg(f + base + nx);
-            if (z > 0) zm[0] = __ldg(f + base - nxy);
-            if (z + 1 < nz) zp[0] = __ldg(f + base + nxy);
         }
-        const float xl = x0 > 0 ? __ldg(f + base - 1) : 0.f;
-        const float xr = x0 + V < nx ? __ldg(f + base + V) : 0.f;
-        uint64_t out[V];
-#pragma unroll
-        for (int j = 0; j < V; j++) {
-            const uint32_t x = x0 + j;
-            const uint32_t u = (uint32_t)(base + j);
-            float fb = c[j];
-            uint32_t b = u;
-            if (!isfinite(fb)) raise_status(status, ST_NONFINITE);
-            // candidates in ascending index order; `before` settles ties
-            if (z > 0 && before(zm[j], u - (uint32_t)nxy, fb, b)) fb = zm[j], b = u - (uint32_t)nxy;
-            if (y > 0 && before(ym[j], u - nx, fb, b)) fb = ym[j], b = u - nx;
-            if (x > 0) {
-                const float w = j > 0 ? c[j - 1] : xl;
-                if (before(w, u - 1, fb, b)) fb = w, b = u - 1;
+    } else {
+        for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+            if (valid(l)) {
+                const float v = __ldg(f + gid(l));
+                bad |= !isfinite(v);
+                K[l] = order_key(v);
             }
-            if (x + 1 < nx) {
-                const float w = j + 1 < V ? c[j + 1] : xr;
-                if (before(w, u + 1, fb, b)) fb = w, b = u + 1;
-            }
-            if (y + 1 < ny && before(yp[j], u + nx, fb, b)) fb = yp[j], b = u + nx;
-            if (z + 1 < nz && before(zp[j], u + (uint32_t)nxy, fb, b)) fb = zp[j], b = u + (uint32_t)nxy;
-            out[j] = tri_pack(u, b);
-        }
-        if constexpr (V == 4) {
-            ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(W + base);
-            dst[0] = make_ulonglong2(out[0], out[1]);
-            dst[1] = make_ulonglong2(out[2], out[3]);
-        } else {
-            W[base] = out[0];
         }
     }
-}
+    if (bad) raise_status(status, ST_NONFINITE);
+    __syncthreads();
 
-// ------------------------------------------------------------- k_descend
-//
-// Pointer jumping along the descent links: every vertex inside a branch,
-// T[u] = (u, v), moves v down the chain of such links towards the minimum
-// that steepest descent reaches, T[u] = (u, m(u)). Each replacement keeps a
-// valid triplet (m(u) comes before u and is joined to it below f(u)), and
-// concurrent replacements only shorten chains, so threads may read entries
-// that others are rewriting. A thread takes at most `hops` steps per round;
-// if any thread stopped early *more is set and the host runs another round
-// (each round multiplies the jump length, so the rounds are logarithmic).
-__global__ void __launch_bounds__(256) k_descend(uint64_t *W, uint64_t n, uint32_t hops, uint32_t *more,
-                                                 const uint32_t *status)
-{
-    if (*status) return;
-    bool unfinished = false;
-    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < n; u += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t T = ld_tri(W + u);
-        if (tri_s(T) != (uint32_t)u || tri_v(T) == (uint32_t)u) continue;  // a minimum
-        uint32_t x = tri_v(T);
-        uint32_t h = 0;
+    // 2. seed: T[l] = (l, first vertex of the closed in-tile neighbourhood)
+    for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+        if (!valid(l)) continue;
+        const uint32_t lx = lxo(l), ly = lyo(l), lz = lzo(l);
+        uint32_t b = l, kb = K[l];
+        // candidates in ascending local index order: an earlier id wins ties,
+        // so an earlier candidate replaces b only if strictly lower
+        if (lz > 0 && K[l - TX * TY] <= kb) b = l - TX * TY, kb = K[b];
+        if (ly > 0 && K[l - TX] <= kb && (K[l - TX] < kb || l - TX < b)) b = l - TX, kb = K[b];
+        if (lx > 0 && K[l - 1] <= kb && (K[l - 1] < kb || l - 1 < b)) b = l - 1, kb = K[b];
+        if (lx + 1 < wx && K[l + 1] < kb) b = l + 1, kb = K[b];
+        if (ly + 1 < wy && K[l + TX] < kb) b = l + TX, kb = K[b];
+        if (lz + 1 < wz && K[l + TX * TY] < kb) b = l + TX * TY, kb = K[b];
+        T[l] = sm_pack(l, b);
+    }
+    __syncthreads();
+
+    // 3. pointer jumping along the descent links (concurrent jumps only
+    //    shorten chains, so racing readers stay correct)
+    {
+        volatile uint32_t *vT = T;
+        for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+            if (!valid(l)) continue;
+            const uint32_t w = vT[l];
+            if (sm_v(w) == l) continue;  // a minimum
+            uint32_t x = sm_v(w);
+            for (uint32_t h = 0; h < (uint32_t)TV; h++) {
+                const uint32_t wx_ = vT[x];
+                if (sm_v(wx_) == x) break;
+                x = sm_v(wx_);
+            }
+            if (x != sm_v(w)) vT[l] = sm_pack(l, x);
+        }
+    }
+    __syncthreads();
+
+    // 4a. list the in-tile edges to the +x, +y, +z neighbours whose ends
+    //     descend to different minima (warp-aggregated appends)
+    for (uint32_t l0 = 0; l0 < TV; l0 += NT) {
+        const uint32_t l = l0 + threadIdx.x;
+        uint32_t mask = 0;
+        if (valid(l)) {
+            const uint32_t dl = sm_v(T[l]);  // descent minimum (l itself for a minimum)
+            const uint32_t lx = lxo(l), ly = lyo(l), lz = lzo(l);
+            if (lx + 1 < wx && sm_v(T[l + 1]) != dl) mask |= 1;
+            if (ly + 1 < wy && sm_v(T[l + TX]) != dl) mask |= 2;
+            if (lz + 1 < wz && sm_v(T[l + TX * TY]) != dl) mask |= 4;
+        }
+        const uint32_t cnt = __popc(mask);
+        uint32_t incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t wbase = 0;
+        if (lane == 31 && tot) wbase = atomicAdd(&s_ntask, tot);
+        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+        uint32_t pos = wbase + incl - cnt;
+        for (int d = 0; d < 3; d++)
+            if (mask & (1u << d)) task[pos++] = (uint16_t)((l << 2) | d);
+    }
+    __syncthreads();
+
+    // 4b. run the merges (Algorithm 3), one climb step per converged
+    //     iteration; idle lanes fetch the next task
+    {
+        const uint32_t ntask = s_ntask;
+        const volatile uint32_t *vT = T;
+        bool busy = false, cu = false, cv = false, ok = true, drained = false;
+        uint32_t S = 0, kS = 0, u = 0, v = 0, Tu = 0, Tv = 0;
+        uint32_t steps = 0;
         for (;;) {
-            const uint64_t Tx = ld_tri(W + x);
-            if (tri_s(Tx) != x || tri_v(Tx) == x) break;  // x is a minimum
-            x = tri_v(Tx);
-            if (++h == hops) {
-                unfinished = true;
-                break;
+            const uint32_t idle = __ballot_sync(0xffffffffu, !busy);
+            if (idle && !drained) {
+                uint32_t tb = 0;
+                const uint32_t leader = __ffs(idle) - 1;
+                if (lane == leader) tb = atomicAdd(&s_next, __popc(idle));
+                tb = __shfl_sync(0xffffffffu, tb, leader);
+                drained = tb + __popc(idle) >= ntask;
+                if (!busy) {
+                    const uint32_t t = tb + __popc(idle & ((1u << lane) - 1u));
+                    if (t < ntask) {
+                        const uint32_t code = task[t];
+                        const uint32_t l = code >> 2, d = code & 3;
+                        const uint32_t w = l + (d == 0 ? 1u : d == 1 ? (uint32_t)TX : (uint32_t)(TX * TY));
+                        const uint32_t kl = K[l], kw = K[w];
+                        if (kbefore(kw, w, kl, l)) S = l, kS = kl;
+                        else S = w, kS = kw;
+                        // descent minimum: an inner vertex's target; a
+                        // minimum (whose entry other merges may have linked
+                        // already, s != itself) stands for itself
+                        const uint32_t Tl = vT[l], Tw = vT[w];
+                        u = sm_s(Tl) == l ? sm_v(Tl) : l;
+                        v = sm_s(Tw) == w ? sm_v(Tw) : w;
+                        busy = cu = cv = true;
+                        steps = 0;
+                    }
+                }
+            }
+            if (!__any_sync(0xffffffffu, busy)) break;
+            if (busy) {
+                // one step of each unfinished climb (links whose saddle is at
+                // or below S are followed; a root stops the climb)
+                if (cu) {
+                    Tu = vT[u];
+                    const uint32_t s = sm_s(Tu);
+                    if (Tu == sm_pack(u, u) || (s != S && !kbefore(K[s], s, kS, S))) cu = false;
+                    else u = sm_v(Tu);
+                }
+                if (cv) {
+                    Tv = vT[v];
+                    const uint32_t s = sm_s(Tv);
+                    if (Tv == sm_pack(v, v) || (s != S && !kbefore(K[s], s, kS, S))) cv = false;
+                    else v = sm_v(Tv);
+                }
+                if (++steps > kMergeStepLimit) {
+                    ok = false;
+                    busy = false;
+                } else if (!cu && !cv) {
+                    if (u == v) {
+                        busy = false;
+                    } else {
+                        if (kbefore(K[v], v, K[u], u)) {
+                            const uint32_t x = u;
+                            u = v;
+                            v = x;
+                            const uint32_t y = Tu;
+                            Tu = Tv;
+                            Tv = y;
+                        }
+                        if (atomicCAS(T + v, Tv, sm_pack(S, u)) == Tv) {
+                            if (Tv == sm_pack(v, v)) {
+                                busy = false;
+                            } else {  // re-insert the displaced link
+                                S = sm_s(Tv);
+                                kS = K[S];
+                                v = sm_v(Tv);
+                            }
+                        }
+                        cu = cv = busy;
+                    }
+                }
             }
         }
-        if (x != tri_v(T)) st_tri(W + u, tri_pack((uint32_t)u, x));
+        if (!ok) raise_status(status, ST_TIMEOUT);
     }
-    if (unfinished) *more = 1u;
-}
+    __syncthreads();
 
-// ---------------------------------------------------------------- k_merge
-//
-// The edge loop of Algorithm 1. Thread u takes the edges to its +x, +y, +z
-// neighbours. For an edge (a, b) with upper end S (the later of the two in
-// the vertex order), Algorithm 1 calls Merge(S, S, lower end). After
-// k_descend both ends point at their descent minima, which are joined to
-// them below S, so the merge starts from those minima; if the two minima
-// coincide the edge is already represented and is skipped (this covers the
-// descent seed edges). Inner-branch entries are never CAS targets (a merge
-// at level S only moves vertices that are deepest below S), so they stay
-// stable while this kernel runs and can be read once up front.
-__device__ __forceinline__ uint32_t descent_root(uint64_t T, uint32_t x)
-{
-    return (tri_s(T) == x && tri_v(T) != x) ? tri_v(T) : x;
-}
+    // 5. repair (Algorithm 5): branch minima first, then inner vertices
+    bool rep_ok = true;
+    for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+        if (!valid(l)) continue;
+        const uint32_t w = T[l];
+        const uint32_t s = sm_s(w);
+        if (s == l) continue;
+        const uint32_t r = sm_rep<TV>(T, K, sm_v(w), s, K[s], rep_ok);
+        if (r != sm_v(w)) T[l] = sm_pack(s, r);
+    }
+    __syncthreads();
+    for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+        if (!valid(l)) continue;
+        const uint32_t w = T[l];
+        if (sm_s(w) != l || sm_v(w) == l) continue;
+        const uint32_t r = sm_rep<TV>(T, K, sm_v(w), l, K[l], rep_ok);
+        if (r != sm_v(w)) T[l] = sm_pack(l, r);
+    }
+    if (!rep_ok) raise_status(status, ST_TIMEOUT);
+    __syncthreads();
 
-__global__ void __launch_bounds__(256) k_merge(uint64_t *W, const float *__restrict__ f, uint32_t nx, uint32_t ny,
-                                               uint32_t nz, uint64_t n, uint32_t *status)
-{
-    if (*status) return;
-    const uint32_t nxy = nx * ny;
-    for (uint64_t uu = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; uu < n;
-         uu += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = (uint32_t)uu;
-        const uint32_t x = u % nx, y = (u / nx) % ny, z = u / nxy;
-        const float fu = __ldg(f + u);
-        const uint32_t du = descent_root(ld_tri(W + u), u);
-        uint32_t nb[3];
-        int k = 0;
-        if (x + 1 < nx) nb[k++] = u + 1;
-        if (y + 1 < ny) nb[k++] = u + nx;
-        if (z + 1 < nz) nb[k++] = u + nxy;
-        for (int j = 0; j < k; j++) {
-            const uint32_t w = nb[j];
-            const uint32_t dw = descent_root(ld_tri(W + w), w);
-            if (dw == du) continue;
-            const uint32_t S = before(__ldg(f + w), w, fu, u) ? u : w;
-            if (!merge(W, f, S, du, dw)) raise_status(status, ST_TIMEOUT);
+    // 6. write the tile's triplets with global ids (coalesced rows)
+    if (vec) {
+        for (uint32_t q = threadIdx.x; q < TV / 2; q += NT) {
+            const uint32_t l = 2 * q;
+            if (!valid(l)) continue;
+            const uint32_t T0 = T[l], T1 = T[l + 1];
+            *reinterpret_cast<ulonglong2 *>(W + gid(l)) = make_ulonglong2(
+                tri_pack(gid(sm_s(T0)), gid(sm_v(T0))), tri_pack(gid(sm_s(T1)), gid(sm_v(T1))));
+        }
+    } else {
+        for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+            if (!valid(l)) continue;
+            const uint32_t w = T[l];
+            W[gid(l)] = tri_pack(gid(sm_s(w)), gid(sm_v(w)));
         }
     }
+}
+
+// ---------------------------------------------------------------- k_cross
+//
+// The rest of the edge loop of Algorithm 1: the edges between neighbouring
+// tiles, merged with 64-bit CAS on the global triplets (Algorithms 2, 3).
+// CTA t takes the edges from tile t to its +x, +y, +z neighbour tiles, so
+// the climbs of one CTA stay mostly within a few tiles' entries (L2 reuse).
+// A merge for edge (a, b) at level S = the later of a, b starts at a and b
+// themselves; their tile triplets lead to the tile-local deepest vertices.
+template <int LX, int LY, int LZ>
+__global__ void __launch_bounds__(256) k_cross(uint64_t *W, const float *__restrict__ f, uint32_t nx, uint32_t ny,
+                                               uint32_t nz, uint32_t ntx, uint32_t nty, uint32_t *status)
+{
+    if (*status) return;
+    using TS = Tile<LX, LY, LZ>;
+    constexpr uint32_t TX = TS::TX, TY = TS::TY, TZ = TS::TZ;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+    const uint32_t wx = min(TX, nx - x0), wy = min(TY, ny - y0), wz = min(TZ, nz - z0);
+    const uint32_t nxy = nx * ny;
+    const uint32_t base = z0 * nxy + y0 * nx + x0;
+    const uint32_t cx = (x0 + TX < nx) ? wy * wz : 0;
+    const uint32_t cy = (y0 + TY < ny) ? wx * wz : 0;
+    const uint32_t cz = (z0 + TZ < nz) ? wx * wy : 0;
+    bool ok = true;
+    for (uint32_t e = threadIdx.x; e < cx + cy + cz; e += blockDim.x) {
+        uint32_t a, b;
+        if (e < cx) {
+            a = base + (e / wy) * nxy + (e % wy) * nx + (TX - 1);
+            b = a + 1;
+        } else if (e < cx + cy) {
+            const uint32_t k = e - cx;
+            a = base + (k / wx) * nxy + (TY - 1) * nx + (k % wx);
+            b = a + nx;
+        } else {
+            const uint32_t k = e - cx - cy;
+            a = base + (TZ - 1) * nxy + (k / wx) * nx + (k % wx);
+            b = a + nxy;
+        }
+        const uint32_t S = before(__ldg(f + b), b, __ldg(f + a), a) ? a : b;
+        ok &= merge(W, f, S, a, b);
+    }
+    if (!ok) raise_status(status, ST_TIMEOUT);
 }
 
 // --------------------------------------------------------------- k_repair
@@ -187,6 +383,9 @@ __global__ void __launch_bounds__(256) k_merge(uint64_t *W, const float *__restr
 // chase that reads a freshly repaired entry reaches the same answer sooner.
 // mode 0 repairs branch minima (s != u), mode 1 the inner vertices
 // (s == u != v); running mode 0 first leaves the chains of mode 1 minimal.
+// Because every rewrite keeps a link on the same chain, a stale cached copy of
+// an entry is still a valid (longer) way to the same answer, so the chases
+// use ordinary L1-cached loads.
 __global__ void __launch_bounds__(256) k_repair(uint64_t *W, const float *__restrict__ f, uint64_t n, int mode,
                                                 uint32_t *status)
 {
@@ -194,11 +393,11 @@ __global__ void __launch_bounds__(256) k_repair(uint64_t *W, const float *__rest
     for (uint64_t uu = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; uu < n;
          uu += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t u = (uint32_t)uu;
-        const uint64_t T = ld_tri(W + u);
+        const uint64_t T = W[u];
         const uint32_t s = tri_s(T), t = tri_v(T);
         if (mode == 0 ? (s == u) : (s != u || t == u)) continue;
         uint32_t steps = 0;
-        const uint32_t r = representative(W, f, t, s, __ldg(f + s), steps);
+        const uint32_t r = representative_cached(W, f, t, s, __ldg(f + s), steps);
         if (steps > kChaseLimit) {
             raise_status(status, ST_TIMEOUT);
             continue;
@@ -216,41 +415,41 @@ static int grid_for(uint64_t work, int threads)
     return (int)(want < cap ? (want ? want : 1) : cap);
 }
 
+// Tile shape 32 x 16 x 16: 8192 vertices, 112 KiB of shared memory, two
+// CTAs of 1024 threads per SM.
+constexpr int kLX = 5, kLY = 4, kLZ = 4, kTileThreads = 1024;
+
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
                          cudaStream_t st)
 {
+    using TS = Tile<kLX, kLY, kLZ>;
     const uint64_t n = (uint64_t)nx * ny * nz;
-    const bool vec = (nx % 4 == 0) && ((uintptr_t)f % 16 == 0) && ((uintptr_t)W % 16 == 0);
-    const uint32_t nxq = vec ? nx / 4 : nx;
-    const uint32_t nthreads = nxq * ny * nz;
+    const int vec = (nx % 4 == 0) && ((uintptr_t)f % 16 == 0) && ((uintptr_t)W % 16 == 0);
+    const uint32_t ntx = (nx + TS::TX - 1) / TS::TX, nty = (ny + TS::TY - 1) / TS::TY,
+                   ntz = (nz + TS::TZ - 1) / TS::TZ;
+    const uint64_t ntiles = (uint64_t)ntx * nty * ntz;
+    const size_t smem = TS::kSmem;
     cudaError_t e;
+    static bool attr_done = false;
+    if (!attr_done) {
+        e = cudaFuncSetAttribute(k_tile<kLX, kLY, kLZ, kTileThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_tile<kLX, kLY, kLZ, kTileThreads>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
     {
-        PhaseScope ps(kInit, st);
-        if (vec)
-            k_init<4><<<grid_for(nthreads, 256), 256, 0, st>>>(f, W, nx, ny, nz, nxq, nthreads, ws.status);
-        else
-            k_init<1><<<grid_for(nthreads, 256), 256, 0, st>>>(f, W, nx, ny, nz, nxq, nthreads, ws.status);
+        PhaseScope ps(kTile, st);
+        k_tile<kLX, kLY, kLZ, kTileThreads><<<(unsigned)ntiles, kTileThreads, smem, st>>>(f, W, nx, ny, nz, ntx,
+                                                                                         nty, vec, ws.status);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
-        // descent rounds: at most ~log_{hops}(n) + 2 of them
-        PhaseScope ps(kDescend, st);
-        for (int round = 0; round < 40; round++) {
-            if ((e = cudaMemsetAsync(ws.more, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
-            k_descend<<<grid_for(n, 256), 256, 0, st>>>(W, n, 64, ws.more, ws.status);
-            count_launch();
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            uint32_t more = 0;
-            if ((e = cudaMemcpyAsync(&more, ws.more, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-                return e;
-            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-            if (!more) break;
-        }
-    }
-    {
         PhaseScope ps(kMerge, st);
-        k_merge<<<grid_for(n, 256), 256, 0, st>>>(W, f, nx, ny, nz, n, ws.status);
+        k_cross<kLX, kLY, kLZ><<<(unsigned)ntiles, 256, 0, st>>>(W, f, nx, ny, nz, ntx, nty, ws.status);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -130,4 +130,20 @@ __device__ __forceinline__ uint32_t representative(const uint64_t *W, const floa
     }
 }
 
+// The same chase with ordinary (L1-cacheable) loads, for passes in which the
+// entries only ever move further along their own chains (repair): a stale
+// copy then still leads to the same representative.
+__device__ __forceinline__ uint32_t representative_cached(const uint64_t *W, const float *f, uint32_t x, uint32_t S,
+                                                          float fS, uint32_t &steps)
+{
+    for (;;) {
+        const uint64_t T = W[x];
+        const uint32_t s = tri_s(T), t = tri_v(T);
+        if (s == x && t == x) return x;
+        if (s != S && !before(__ldg(f + s), s, fS, S)) return x;
+        x = t;
+        if (++steps > kChaseLimit) return x;
+    }
+}
+
 }  // namespace mt
