@@ -26,17 +26,32 @@ namespace mt {
 // 32-bit keys whose unsigned order is the float order (-0 and +0 share one
 // key), so a vertex comparison is an integer comparison of (key, id).
 //
-// Within the tile the initial tree is seeded along steepest descent:
-// T[l] = (l, lln(l)) with lln(l) the first vertex of l's closed in-tile
-// neighbourhood (a normalised triplet of the graph of descent edges); pointer
-// jumping then moves every inner vertex straight to the minimum its descent
-// reaches, and an edge whose two ends reach the same minimum needs no merge.
+// Seed. T[l] = (l, lln(l)), lln(l) the first vertex of l's closed in-tile
+// neighbourhood (a normalised triplet of the graph of steepest-descent
+// edges); pointer jumping then moves every inner vertex straight to the
+// minimum its descent reaches. An edge whose ends reach the same minimum
+// needs no merge.
 //
-// The merges themselves are organised for SIMT execution: the CTA first
-// lists the edges that need a merge (task list in shared memory), then every
-// lane pulls tasks dynamically and advances its merge by one climb step per
-// iteration of a loop in which the whole warp stays converged, so lanes with
-// short and long climbs do not serialise each other.
+// Level buckets and shortcuts. The remaining edges are merged in NB rounds
+// by the level of their upper end S (NB buckets of about equal size, cut from
+// a histogram of the tile's keys); within a round the order is free, as
+// Algorithm 1 allows. SC[m] is a shortcut for minimum m: the vertex m's climb
+// reaches through the links whose saddle lies in buckets before the current
+// one, i.e. the deepest vertex of m's component below the round. Those links
+// do not change during a round (a merge at level S only displaces links above
+// S), so a shortcut is computed on first use in a round and stored with the
+// round number in its top bits. An edge (S, a, c) starts its climbs at SC[a]
+// and SC[c] (both joined to a, c below S), and when they coincide the ends are
+// already connected below S and the edge is settled by two shared-memory
+// loads, as about nine edges in ten are on these fields. The others are
+// queued and merged together once the bucket's scan is done, so that the
+// lanes of a warp run their merges side by side instead of one after another.
+//
+// Repair. Right after round b no later merge can change a component below
+// the levels of bucket b, so every inner vertex l of bucket b gets its final
+// tile triplet (l, deepest vertex below l) by a short climb from its
+// minimum's shortcut (Algorithms 4 and 5). Branch minima are repaired at the
+// end.
 //
 // What leaves the kernel is, for every vertex, its triplet in the subgraph
 // induced by its tile: a valid normalised triplet tree of the full grid minus
@@ -45,10 +60,14 @@ template <int LX, int LY, int LZ>
 struct Tile {
     static constexpr int TX = 1 << LX, TY = 1 << LY, TZ = 1 << LZ;
     static constexpr int TV = TX * TY * TZ;
-    static_assert(TV <= 16384, "tasks pack a local id and a direction into 16 bits");
+    static_assert(TV <= 65536, "local ids are 16-bit");
     static_assert(TX % 4 == 0, "rows are loaded as float4");
-    // shared memory: keys, triplets (4 B each) and up to 3 tasks (2 B each)
-    static constexpr size_t kSmem = (size_t)TV * (4 + 4 + 6);
+    static constexpr int kBins = 1024;
+    static constexpr int kQueue = 2048;  // deferred merges per flush
+    // shared memory: keys + triplets (4 B each), shortcuts + bucket-sorted
+    // vertex list (2 B each), merge queue (aliased by the key histogram)
+    static constexpr size_t kSmem = (size_t)TV * (4 + 4 + 2 + 2) + (size_t)kQueue * 4;
+    static_assert(kQueue >= kBins, "the histogram lives in the queue buffer");
 };
 
 __device__ __forceinline__ uint32_t sm_pack(uint32_t s, uint32_t v) { return (s << 16) | v; }
@@ -67,16 +86,16 @@ __device__ __forceinline__ bool kbefore(uint32_t ka, uint32_t a, uint32_t kb, ui
     return ka < kb || (ka == kb && a < b);
 }
 
-// Representative (Algorithm 4) in the tile's tree at level (kS, S).
-// Every link leads to an earlier vertex, so a chain is shorter than the tile;
-// a longer one can only come from a corrupted tree and clears ok.
+// Climb (Algorithm 3 / 4) in the tile's tree from x through links whose
+// saddle is at or below (kS, S); a root stops it. Chains lead to ever earlier
+// vertices, so a walk longer than the tile means a corrupted tree (ok=false).
 template <int TV>
-__device__ __forceinline__ uint32_t sm_rep(const uint32_t *T, const uint32_t *K, uint32_t x, uint32_t S,
-                                           uint32_t kS, bool &ok)
+__device__ __forceinline__ uint32_t sm_climb(const uint32_t *T, const uint32_t *K, uint32_t x, uint32_t S,
+                                             uint32_t kS, uint32_t &w, bool &ok)
 {
     const volatile uint32_t *vT = T;
     for (uint32_t h = 0; h < (uint32_t)TV; h++) {
-        const uint32_t w = vT[x];
+        w = vT[x];
         if (w == sm_pack(x, x)) return x;
         const uint32_t s = sm_s(w);
         if (s != S && !kbefore(K[s], s, kS, S)) return x;
@@ -86,20 +105,61 @@ __device__ __forceinline__ uint32_t sm_rep(const uint32_t *T, const uint32_t *K,
     return x;
 }
 
-template <int LX, int LY, int LZ, int NT>
+// Merge (Algorithm 3) on the tile's shared-memory tree, lock-free with 32-bit
+// CAS (Algorithm 2): climb a and c to their deepest vertices below S; if they
+// differ, link the later one under the earlier at S and re-insert the link
+// it held before (a displaced root carries none); on a failed CAS climb again.
+template <int TV>
+__device__ __forceinline__ void sm_merge(uint32_t *T, const uint32_t *K, uint32_t S, uint32_t kS, uint32_t a,
+                                         uint32_t c, bool &ok)
+{
+    uint32_t u = a, v = c;
+    for (uint32_t it = 0; it < kMergeStepLimit; it++) {
+        uint32_t Tu, Tv;
+        u = sm_climb<TV>(T, K, u, S, kS, Tu, ok);
+        v = sm_climb<TV>(T, K, v, S, kS, Tv, ok);
+        if (!ok || u == v) return;
+        if (kbefore(K[v], v, K[u], u)) {
+            const uint32_t x = u;
+            u = v;
+            v = x;
+            const uint32_t y = Tu;
+            Tu = Tv;
+            Tv = y;
+        }
+        if (atomicCAS(T + v, Tv, sm_pack(S, u)) == Tv) {
+            if (Tv == sm_pack(v, v)) return;
+            S = sm_s(Tv);
+            kS = K[S];
+            v = sm_v(Tv);
+        }
+    }
+    ok = false;
+}
+
+template <int LX, int LY, int LZ, int NT, int NB>
 __global__ void __launch_bounds__(NT, 2) k_tile(const float *__restrict__ f, uint64_t *__restrict__ W, uint32_t nx,
                                                 uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty, int vec,
                                                 uint32_t *status)
 {
     using TS = Tile<LX, LY, LZ>;
-    constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV;
+    constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV, BINS = TS::kBins, Q = TS::kQueue;
+    constexpr uint32_t IDB = LX + LY + LZ;  // bits of a local id
+    constexpr uint32_t IDM = (1u << IDB) - 1u;
+    static_assert(NT >= BINS, "one histogram bin per thread");
+    static_assert(IDB + 3 <= 16 && NB <= 8, "a shortcut packs a local id and a round number into 16 bits");
     extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *K = smem;       // order keys
-    uint32_t *T = smem + TV;  // triplets (s << 16) | v
-    uint16_t *task = reinterpret_cast<uint16_t *>(smem + 2 * TV);
-    __shared__ uint32_t s_ntask, s_next;
+    uint32_t *K = smem;                                           // order keys
+    uint32_t *T = smem + TV;                                      // triplets (s << 16) | v
+    uint16_t *SC = reinterpret_cast<uint16_t *>(smem + 2 * TV);   // shortcuts (round << IDB) | vertex
+    uint16_t *vlist = SC + TV;                                    // vertices sorted by bucket
+    uint32_t *queue = reinterpret_cast<uint32_t *>(vlist + TV);   // deferred merges (S << 16) | c
+    uint32_t *hist = queue;                                       // key histogram (before the rounds)
+    __shared__ uint8_t s_bmap[BINS];                              // histogram bin -> bucket
+    __shared__ uint32_t s_kmin, s_kmax, s_nvalid, s_qlen, s_warp[NT / 32];
+    __shared__ uint32_t s_boff[NB + 1], s_bcur[NB];
 
-    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t tile = blockIdx.x;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
@@ -114,18 +174,27 @@ __global__ void __launch_bounds__(NT, 2) k_tile(const float *__restrict__ f, uin
     auto gid = [&](uint32_t l) {
         return (uint32_t)(base + (uint64_t)lzo(l) * nxy + (uint64_t)lyo(l) * nx + lxo(l));
     };
-    if (threadIdx.x == 0) s_ntask = 0, s_next = 0;
+    if (threadIdx.x == 0) {
+        s_kmin = 0xFFFFFFFFu, s_kmax = 0, s_qlen = 0;
+        s_nvalid = wx * wy * wz;
+    }
+    if (threadIdx.x < NB) s_bcur[threadIdx.x] = 0;
+    for (uint32_t i = threadIdx.x; i < (uint32_t)BINS; i += NT) hist[i] = 0;
+    __syncthreads();
 
     // 1. load the tile's values (rows of TX floats) as order keys
     bool bad = false;
+    uint32_t kmin = 0xFFFFFFFFu, kmax = 0;
     if (vec) {
         for (uint32_t q = threadIdx.x; q < TV / 4; q += NT) {
             const uint32_t l = 4 * q;
             if (lxo(l) < wx && lyo(l) < wy && lzo(l) < wz) {
                 const float4 v = __ldg(reinterpret_cast<const float4 *>(f + gid(l)));
                 bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
-                *reinterpret_cast<uint4 *>(K + l) = make_uint4(order_key(v.x), order_key(v.y), order_key(v.z),
-                                                              order_key(v.w));
+                const uint4 k = make_uint4(order_key(v.x), order_key(v.y), order_key(v.z), order_key(v.w));
+                kmin = min(kmin, min(min(k.x, k.y), min(k.z, k.w)));
+                kmax = max(kmax, max(max(k.x, k.y), max(k.z, k.w)));
+                *reinterpret_cast<uint4 *>(K + l) = k;
             }
         }
     } else {
@@ -133,18 +202,34 @@ __global__ void __launch_bounds__(NT, 2) k_tile(const float *__restrict__ f, uin
             if (valid(l)) {
                 const float v = __ldg(f + gid(l));
                 bad |= !isfinite(v);
-                K[l] = order_key(v);
+                const uint32_t k = order_key(v);
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+                K[l] = k;
             }
         }
     }
     if (bad) raise_status(status, ST_NONFINITE);
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    if (lane == 0) {
+        atomicMin(&s_kmin, kmin);
+        atomicMax(&s_kmax, kmax);
+    }
     __syncthreads();
 
-    // 2. seed: T[l] = (l, first vertex of the closed in-tile neighbourhood)
+    // 2. seed: T[l] = (l, first vertex of the closed in-tile neighbourhood);
+    //    key histogram for the level buckets
+    const uint32_t kmin_t = s_kmin;
+    const float bscale = (float)BINS / ((float)(s_kmax - kmin_t) + 1.0f);
+    auto bin_of = [&](uint32_t k) { return min((uint32_t)BINS - 1, (uint32_t)((float)(k - kmin_t) * bscale)); };
     for (uint32_t l = threadIdx.x; l < TV; l += NT) {
         if (!valid(l)) continue;
         const uint32_t lx = lxo(l), ly = lyo(l), lz = lzo(l);
         uint32_t b = l, kb = K[l];
+        atomicAdd(&hist[bin_of(kb)], 1u);
         // candidates in ascending local index order: an earlier id wins ties,
         // so an earlier candidate replaces b only if strictly lower
         if (lz > 0 && K[l - TX * TY] <= kb) b = l - TX * TY, kb = K[b];
@@ -158,13 +243,18 @@ __global__ void __launch_bounds__(NT, 2) k_tile(const float *__restrict__ f, uin
     __syncthreads();
 
     // 3. pointer jumping along the descent links (concurrent jumps only
-    //    shorten chains, so racing readers stay correct)
+    //    shorten chains, so racing readers stay correct); shortcuts start at
+    //    the minima themselves. Bin -> bucket map from the histogram's
+    //    prefix sums (monotone in the key).
     {
         volatile uint32_t *vT = T;
         for (uint32_t l = threadIdx.x; l < TV; l += NT) {
             if (!valid(l)) continue;
             const uint32_t w = vT[l];
-            if (sm_v(w) == l) continue;  // a minimum
+            if (sm_v(w) == l) {
+                SC[l] = (uint16_t)l;
+                continue;
+            }
             uint32_t x = sm_v(w);
             for (uint32_t h = 0; h < (uint32_t)TV; h++) {
                 const uint32_t wx_ = vT[x];
@@ -173,144 +263,142 @@ __global__ void __launch_bounds__(NT, 2) k_tile(const float *__restrict__ f, uin
             }
             if (x != sm_v(w)) vT[l] = sm_pack(l, x);
         }
-    }
-    __syncthreads();
-
-    // 4a. list the in-tile edges to the +x, +y, +z neighbours whose ends
-    //     descend to different minima (warp-aggregated appends)
-    for (uint32_t l0 = 0; l0 < TV; l0 += NT) {
-        const uint32_t l = l0 + threadIdx.x;
-        uint32_t mask = 0;
-        if (valid(l)) {
-            const uint32_t dl = sm_v(T[l]);  // descent minimum (l itself for a minimum)
-            const uint32_t lx = lxo(l), ly = lyo(l), lz = lzo(l);
-            if (lx + 1 < wx && sm_v(T[l + 1]) != dl) mask |= 1;
-            if (ly + 1 < wy && sm_v(T[l + TX]) != dl) mask |= 2;
-            if (lz + 1 < wz && sm_v(T[l + TX * TY]) != dl) mask |= 4;
-        }
-        const uint32_t cnt = __popc(mask);
-        uint32_t incl = cnt;
+        const uint32_t c = threadIdx.x < (uint32_t)BINS ? hist[threadIdx.x] : 0u;
+        uint32_t incl = c;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= (uint32_t)o) incl += y;
         }
-        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-        uint32_t wbase = 0;
-        if (lane == 31 && tot) wbase = atomicAdd(&s_ntask, tot);
-        wbase = __shfl_sync(0xffffffffu, wbase, 31);
-        uint32_t pos = wbase + incl - cnt;
-        for (int d = 0; d < 3; d++)
-            if (mask & (1u << d)) task[pos++] = (uint16_t)((l << 2) | d);
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        uint32_t before_w = 0;
+        for (uint32_t w = 0; w < warp; w++) before_w += s_warp[w];
+        if (threadIdx.x < (uint32_t)BINS)
+            s_bmap[threadIdx.x] =
+                (uint8_t)min((uint32_t)NB - 1, (uint32_t)(((uint64_t)(before_w + incl - c) * NB) / s_nvalid));
+    }
+    __syncthreads();
+    auto bucket_of = [&](uint32_t k) { return (uint32_t)s_bmap[bin_of(k)]; };
+
+    // 4. counting sort of the vertices by bucket
+    for (uint32_t l = threadIdx.x; l < TV; l += NT)
+        if (valid(l)) atomicAdd(&s_bcur[bucket_of(K[l])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < NB; b++) {
+            s_boff[b] = run;
+            run += s_bcur[b];
+            s_bcur[b] = s_boff[b];
+        }
+        s_boff[NB] = run;
+    }
+    __syncthreads();
+    for (uint32_t l0 = 0; l0 < TV; l0 += NT) {
+        const uint32_t l = l0 + threadIdx.x;
+        const bool ok_l = valid(l);
+        const uint32_t b = ok_l ? bucket_of(K[l]) : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        if (ok_l) {
+            const uint32_t leader = __ffs(peers) - 1;
+            uint32_t pos = 0;
+            if (lane == leader) pos = atomicAdd(&s_bcur[b], __popc(peers));
+            pos = __shfl_sync(peers, pos, leader);
+            vlist[pos + __popc(peers & ((1u << lane) - 1u))] = (uint16_t)l;
+        }
     }
     __syncthreads();
 
-    // 4b. run the merges (Algorithm 3), one climb step per converged
-    //     iteration; idle lanes fetch the next task
-    {
-        const uint32_t ntask = s_ntask;
-        const volatile uint32_t *vT = T;
-        bool busy = false, cu = false, cv = false, ok = true, drained = false;
-        uint32_t S = 0, kS = 0, u = 0, v = 0, Tu = 0, Tv = 0;
-        uint32_t steps = 0;
-        for (;;) {
-            const uint32_t idle = __ballot_sync(0xffffffffu, !busy);
-            if (idle && !drained) {
-                uint32_t tb = 0;
-                const uint32_t leader = __ffs(idle) - 1;
-                if (lane == leader) tb = atomicAdd(&s_next, __popc(idle));
-                tb = __shfl_sync(0xffffffffu, tb, leader);
-                drained = tb + __popc(idle) >= ntask;
-                if (!busy) {
-                    const uint32_t t = tb + __popc(idle & ((1u << lane) - 1u));
-                    if (t < ntask) {
-                        const uint32_t code = task[t];
-                        const uint32_t l = code >> 2, d = code & 3;
-                        const uint32_t w = l + (d == 0 ? 1u : d == 1 ? (uint32_t)TX : (uint32_t)(TX * TY));
-                        const uint32_t kl = K[l], kw = K[w];
-                        if (kbefore(kw, w, kl, l)) S = l, kS = kl;
-                        else S = w, kS = kw;
-                        // descent minimum: an inner vertex's target; a
-                        // minimum (whose entry other merges may have linked
-                        // already, s != itself) stands for itself
-                        const uint32_t Tl = vT[l], Tw = vT[w];
-                        u = sm_s(Tl) == l ? sm_v(Tl) : l;
-                        v = sm_s(Tw) == w ? sm_v(Tw) : w;
-                        busy = cu = cv = true;
-                        steps = 0;
-                    }
-                }
+    // 5. rounds over the level buckets
+    bool ok = true;
+    volatile uint32_t *vT = T;
+    volatile uint16_t *vSC = SC;
+    for (int b = 0; b < NB; b++) {
+        // shortcut of minimum m for round b: climb through the links whose
+        // saddle lies in an earlier bucket, from where round (SC >> IDB) left it
+        auto shortcut = [&](uint32_t m) -> uint32_t {
+            const uint32_t sc = vSC[m];
+            uint32_t x = sc & IDM;
+            if ((sc >> IDB) == (uint32_t)b) return x;
+            for (uint32_t h = 0; h < (uint32_t)TV; h++) {
+                const uint32_t w = vT[x];
+                if (w == sm_pack(x, x) || bucket_of(K[sm_s(w)]) >= (uint32_t)b) break;
+                x = sm_v(w);
             }
-            if (!__any_sync(0xffffffffu, busy)) break;
-            if (busy) {
-                // one step of each unfinished climb (links whose saddle is at
-                // or below S are followed; a root stops the climb)
-                if (cu) {
-                    Tu = vT[u];
-                    const uint32_t s = sm_s(Tu);
-                    if (Tu == sm_pack(u, u) || (s != S && !kbefore(K[s], s, kS, S))) cu = false;
-                    else u = sm_v(Tu);
-                }
-                if (cv) {
-                    Tv = vT[v];
-                    const uint32_t s = sm_s(Tv);
-                    if (Tv == sm_pack(v, v) || (s != S && !kbefore(K[s], s, kS, S))) cv = false;
-                    else v = sm_v(Tv);
-                }
-                if (++steps > kMergeStepLimit) {
-                    ok = false;
-                    busy = false;
-                } else if (!cu && !cv) {
-                    if (u == v) {
-                        busy = false;
-                    } else {
-                        if (kbefore(K[v], v, K[u], u)) {
-                            const uint32_t x = u;
-                            u = v;
-                            v = x;
-                            const uint32_t y = Tu;
-                            Tu = Tv;
-                            Tv = y;
-                        }
-                        if (atomicCAS(T + v, Tv, sm_pack(S, u)) == Tv) {
-                            if (Tv == sm_pack(v, v)) {
-                                busy = false;
-                            } else {  // re-insert the displaced link
-                                S = sm_s(Tv);
-                                kS = K[S];
-                                v = sm_v(Tv);
-                            }
-                        }
-                        cu = cv = busy;
-                    }
-                }
+            vSC[m] = (uint16_t)(((uint32_t)b << IDB) | x);
+            return x;
+        };
+        const uint32_t i0 = s_boff[b], i1 = s_boff[b + 1];
+        // 5a. scan the edges whose upper end S lies in bucket b; queue those
+        //     whose ends are not yet known to be connected below S
+        for (uint32_t i = i0 + threadIdx.x; i < i1; i += NT) {
+            const uint32_t S = vlist[i];
+            const uint32_t TSw = vT[S];
+            if (sm_s(TSw) != S || sm_v(TSw) == S) continue;  // a minimum has no lower neighbour
+            const uint32_t kS = K[S], dS = sm_v(TSw);
+            const uint32_t lx = lxo(S), ly = lyo(S), lz = lzo(S);
+            uint32_t aS = 0xFFFFFFFFu;
+#pragma unroll
+            for (int d = 0; d < 6; d++) {
+                uint32_t w;
+                if (d == 0) { if (lz == 0) continue; w = S - TX * TY; }
+                else if (d == 1) { if (ly == 0) continue; w = S - TX; }
+                else if (d == 2) { if (lx == 0) continue; w = S - 1; }
+                else if (d == 3) { if (lx + 1 >= wx) continue; w = S + 1; }
+                else if (d == 4) { if (ly + 1 >= wy) continue; w = S + TX; }
+                else { if (lz + 1 >= wz) continue; w = S + TX * TY; }
+                if (!kbefore(K[w], w, kS, S)) continue;  // only edges to lower neighbours
+                const uint32_t Tw = vT[w];
+                // w's minimum: an inner vertex's target, else w itself
+                const uint32_t dw = (sm_s(Tw) == w && sm_v(Tw) != w) ? sm_v(Tw) : w;
+                if (dw == dS) continue;
+                if (aS == 0xFFFFFFFFu) aS = shortcut(dS);
+                const uint32_t aw = shortcut(dw);
+                if (aw == aS) continue;  // already connected below S
+                const uint32_t slot = atomicAdd(&s_qlen, 1u);
+                if (slot < (uint32_t)Q) queue[slot] = (S << 16) | aw;
+                else sm_merge<TV>(T, K, S, kS, aS, aw, ok);  // queue full: merge in place
             }
         }
-        if (!ok) raise_status(status, ST_TIMEOUT);
+        __syncthreads();
+        // 5b. run the queued merges side by side
+        {
+            const uint32_t nq = min(s_qlen, (uint32_t)Q);
+            for (uint32_t i = threadIdx.x; i < nq; i += NT) {
+                const uint32_t e = queue[i];
+                const uint32_t S = e >> 16, c = e & 0xFFFFu;
+                const uint32_t aS = vSC[sm_v(vT[S])] & IDM;  // set in 5a for this round
+                sm_merge<TV>(T, K, S, K[S], aS, c, ok);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_qlen = 0;
+        // 5c. final tile triplets of the inner vertices of bucket b
+        for (uint32_t i = i0 + threadIdx.x; i < i1; i += NT) {
+            const uint32_t l = vlist[i];
+            const uint32_t w = vT[l];
+            if (sm_s(w) != l || sm_v(w) == l) continue;
+            uint32_t wr;
+            const uint32_t r = sm_climb<TV>(T, K, shortcut(sm_v(w)), l, K[l], wr, ok);
+            if (r != sm_v(w)) T[l] = sm_pack(l, r);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
-    // 5. repair (Algorithm 5): branch minima first, then inner vertices
-    bool rep_ok = true;
+    // 6. repair the branch minima (Algorithm 5)
     for (uint32_t l = threadIdx.x; l < TV; l += NT) {
         if (!valid(l)) continue;
-        const uint32_t w = T[l];
+        const uint32_t w = vT[l];
         const uint32_t s = sm_s(w);
-        if (s == l) continue;
-        const uint32_t r = sm_rep<TV>(T, K, sm_v(w), s, K[s], rep_ok);
+        if (s == l) continue;  // inner vertex or root
+        uint32_t wr;
+        const uint32_t r = sm_climb<TV>(T, K, sm_v(w), s, K[s], wr, ok);
         if (r != sm_v(w)) T[l] = sm_pack(s, r);
     }
-    __syncthreads();
-    for (uint32_t l = threadIdx.x; l < TV; l += NT) {
-        if (!valid(l)) continue;
-        const uint32_t w = T[l];
-        if (sm_s(w) != l || sm_v(w) == l) continue;
-        const uint32_t r = sm_rep<TV>(T, K, sm_v(w), l, K[l], rep_ok);
-        if (r != sm_v(w)) T[l] = sm_pack(l, r);
-    }
-    if (!rep_ok) raise_status(status, ST_TIMEOUT);
+    if (!ok) raise_status(status, ST_TIMEOUT);
     __syncthreads();
 
-    // 6. write the tile's triplets with global ids (coalesced rows)
+    // 7. write the tile's triplets with global ids (coalesced rows)
     if (vec) {
         for (uint32_t q = threadIdx.x; q < TV / 2; q += NT) {
             const uint32_t l = 2 * q;
@@ -415,9 +503,9 @@ static int grid_for(uint64_t work, int threads)
     return (int)(want < cap ? (want ? want : 1) : cap);
 }
 
-// Tile shape 32 x 16 x 16: 8192 vertices, 112 KiB of shared memory, two
-// CTAs of 1024 threads per SM.
-constexpr int kLX = 5, kLY = 4, kLZ = 4, kTileThreads = 1024;
+// Tile shape 32 x 16 x 16: 8192 vertices, about 108 KiB of shared memory,
+// two CTAs of 1024 threads per SM; 8 level buckets.
+constexpr int kLX = 5, kLY = 4, kLZ = 4, kTileThreads = 1024, kBuckets = 8;
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
                          cudaStream_t st)
@@ -432,17 +520,17 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
     cudaError_t e;
     static bool attr_done = false;
     if (!attr_done) {
-        e = cudaFuncSetAttribute(k_tile<kLX, kLY, kLZ, kTileThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_tile<kLX, kLY, kLZ, kTileThreads, kBuckets>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_tile<kLX, kLY, kLZ, kTileThreads>,
+        e = cudaFuncSetAttribute(k_tile<kLX, kLY, kLZ, kTileThreads, kBuckets>,
                                  cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     {
         PhaseScope ps(kTile, st);
-        k_tile<kLX, kLY, kLZ, kTileThreads><<<(unsigned)ntiles, kTileThreads, smem, st>>>(f, W, nx, ny, nz, ntx,
+        k_tile<kLX, kLY, kLZ, kTileThreads, kBuckets><<<(unsigned)ntiles, kTileThreads, smem, st>>>(f, W, nx, ny, nz, ntx,
                                                                                          nty, vec, ws.status);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
