@@ -119,6 +119,32 @@ mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, flo
  */
 mt_status mt_sync_status(void *d_ws, void *stream);
 
+/*
+ * Persistence pairs for callers that cannot allocate device memory. The paper
+ * has no counterpart to this call; it exists because some callers may not
+ * obtain a workspace: a host application may own all device memory through
+ * its own pool and forbid further cudaMalloc, or a latency-critical path may
+ * not take the synchronisation and latency of an allocation. It computes the
+ * same pairs, root and count as mt_persistence_pairs (same arguments minus
+ * the workspace) and synchronises `stream` in the same way.
+ *   Scratch: one array of about 1 MiB compiled into libmt. It exists on every
+ *            GPU that loads the library and stays allocated there until the
+ *            process exits. This call allocates and frees nothing.
+ *   Limit:   n <= 2^30 vertices (1024^3); larger grids get MT_ERR_TOO_LARGE
+ *            before anything is enqueued.
+ *   Set-up:  the first call on a device looks up the array's device address
+ *            (cudaGetSymbolAddress, with that device current); make that
+ *            first call before any stream capture begins.
+ *   Sharing: every call uses the same array, which keeps the last call's
+ *            contents (each call clears what must start at zero). Calls that
+ *            overlap on the GPU (other streams, other host threads) race on it
+ *            and must be serialised by the caller.
+ *   Status:  device errors recorded by mt_build_triplets live in that call's
+ *            workspace and are not reported here.
+ */
+mt_status mt_persistence_pairs_noalloc(const float *d_f, const uint64_t *d_W, mt_grid g, uint32_t *d_pairs,
+                                       uint64_t cap, uint64_t *h_npairs, uint32_t *h_root, void *stream);
+
 /* ------------------------------------------------------------- tracing
  * Not part of the paper's method: diagnostics for benchmarks and profiling.
  * When enabled, every step (init, descend, merge, repair, pairs, labels, ...)

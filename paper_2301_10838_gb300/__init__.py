@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     mt_build_triplets,
     mt_components_at,
     mt_persistence_pairs,
+    mt_persistence_pairs_noalloc,
     mt_status_str,
     mt_kernel_launches,
     mt_sync_status,
@@ -31,6 +32,7 @@ __all__ = [
     "mt_build_triplets",
     "mt_components_at",
     "mt_persistence_pairs",
+    "mt_persistence_pairs_noalloc",
     "mt_status_str",
     "mt_sync_status",
     "mt_trace_enable",

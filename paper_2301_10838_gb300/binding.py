@@ -33,6 +33,7 @@ __all__ = [
     "mt_persistence_pairs",
     "mt_components_at",
     "mt_sync_status",
+    "mt_persistence_pairs_noalloc",
     "mt_trace_enable",
     "mt_trace_read",
     "mt_kernel_launches",
@@ -68,6 +69,7 @@ _SIGS = {
     "mt_persistence_pairs": ([_P, _P, Grid, _P, _U64, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_components_at": ([_P, _P, Grid, ctypes.c_float, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_sync_status": ([_P, _P], ctypes.c_int32),
+    "mt_persistence_pairs_noalloc": ([_P, _P, Grid, _P, _U64, _P, _P, _P], ctypes.c_int32),
     "mt_trace_enable": ([ctypes.c_int], None),
     "mt_trace_read": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "mt_kernel_launches": ([], ctypes.c_ulonglong),
@@ -178,6 +180,29 @@ def mt_persistence_pairs(f: torch.Tensor, W: torch.Tensor, pairs: torch.Tensor, 
     if code == -4 and allow_partial:
         return int(npairs.value), int(root.value)
     _check(code, "mt_persistence_pairs", f" npairs={npairs.value} cap={cap}")
+    return int(npairs.value), int(root.value)
+
+
+def mt_persistence_pairs_noalloc(f: torch.Tensor, W: torch.Tensor, pairs: torch.Tensor, stream=None,
+                                 allow_partial: bool = False) -> tuple[int, int]:
+    """mt_persistence_pairs without a workspace: the C call takes its scratch
+    from an array inside libmt (for callers that cannot allocate device
+    memory). Returns (npairs, root); synchronises the stream."""
+    g = grid_of(f)
+    n = f.numel()
+    pf = _dev(f, "f", (torch.float32,))
+    pW = _dev(W, "W", _I64, n)
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must have shape (cap, 2)")
+    cap = int(pairs.shape[0])
+    pp = _dev(pairs, "pairs", _I32) if cap else 0
+    npairs = ctypes.c_uint64(0)
+    root = ctypes.c_uint32(0xFFFFFFFF)
+    code = load().mt_persistence_pairs_noalloc(pf, pW, g, pp, cap, ctypes.byref(npairs), ctypes.byref(root),
+                                               _stream_ptr(stream))
+    if code == -4 and allow_partial:
+        return int(npairs.value), int(root.value)
+    _check(code, "mt_persistence_pairs_noalloc", f" npairs={npairs.value} cap={cap}")
     return int(npairs.value), int(root.value)
 
 
