@@ -138,7 +138,7 @@ mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, flo
         return MT_ERR_INVALID;
     Workspace ws;
     if (!carve_workspace(d_ws, ws_bytes, n, ws)) return MT_ERR_INVALID;
-    if (launch_labels(d_f, d_W, n, t, d_labels, ws, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    if (launch_labels(d_f, d_W, g.nx, g.ny, g.nz, t, d_labels, ws, static_cast<cudaStream_t>(stream)) != cudaSuccess)
         return MT_ERR_CUDA;
     return MT_OK;
 }

@@ -56,14 +56,14 @@ namespace mt {
 // What leaves the kernel is, for every vertex, its triplet in the subgraph
 // induced by its tile: a valid normalised triplet tree of the full grid minus
 // the edges between tiles, which k_cross merges next.
-template <int LX, int LY, int LZ>
+template <int LX, int LY, int LZ, int NT = 512>
 struct Tile {
     static constexpr int TX = 1 << LX, TY = 1 << LY, TZ = 1 << LZ;
     static constexpr int TV = TX * TY * TZ;
     static_assert(TV <= 65536, "local ids are 16-bit");
     static_assert(TX % 4 == 0, "rows are loaded as float4");
-    static constexpr int kBins = 1024;
-    static constexpr int kQueue = 2048;  // deferred merges per flush
+    static constexpr int kBins = NT;     // key histogram, one bin per thread
+    static constexpr int kQueue = 2048 * TV / 8192 > NT ? 2048 * TV / 8192 : NT;  // deferred merges per flush
     // shared memory: keys + triplets (4 B each), shortcuts + bucket-sorted
     // vertex list (2 B each), merge queue (aliased by the key histogram)
     static constexpr size_t kSmem = (size_t)TV * (4 + 4 + 2 + 2) + (size_t)kQueue * 4;
@@ -138,11 +138,11 @@ __device__ __forceinline__ void sm_merge(uint32_t *T, const uint32_t *K, uint32_
 }
 
 template <int LX, int LY, int LZ, int NT, int NB>
-__global__ void __launch_bounds__(NT, 2) k_tile(const float *__restrict__ f, uint64_t *__restrict__ W, uint32_t nx,
+__global__ void __launch_bounds__(NT, 2048 / NT) k_tile(const float *__restrict__ f, uint64_t *__restrict__ W, uint32_t nx,
                                                 uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty, int vec,
                                                 uint32_t *status)
 {
-    using TS = Tile<LX, LY, LZ>;
+    using TS = Tile<LX, LY, LZ, NT>;
     constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV, BINS = TS::kBins, Q = TS::kQueue;
     constexpr uint32_t IDB = LX + LY + LZ;  // bits of a local id
     constexpr uint32_t IDM = (1u << IDB) - 1u;
@@ -463,55 +463,62 @@ __global__ void __launch_bounds__(256) k_cross(uint64_t *W, const float *__restr
 
 // --------------------------------------------------------------- k_repair
 //
-// Repair (Algorithm 5): T[u] = (s, Representative(u, s)) restores
-// minimality. Level comparisons use the vertex order, not values alone:
-// with tied values a saddle s' equal in value to s but after it in the order
-// is not yet part of the sublevel set at s. Concurrent repairs only replace a
-// target by one further along the same chain below the same level, so a
-// chase that reads a freshly repaired entry reaches the same answer sooner.
-// mode 0 repairs branch minima (s != u), mode 1 the inner vertices
-// (s == u != v); running mode 0 first leaves the chains of mode 1 minimal.
-// Because every rewrite keeps a link on the same chain, a stale cached copy of
-// an entry is still a valid (longer) way to the same answer, so the chases
-// use ordinary L1-cached loads.
-__global__ void __launch_bounds__(256) k_repair(uint64_t *W, const float *__restrict__ f, uint64_t n, int mode,
-                                                uint32_t *status)
+// Repair (Algorithm 5) after the cross-tile merges: T[u] = (s, Rep(u, s))
+// restores minimality. Level comparisons use the vertex order, not values
+// alone: with tied values a saddle s' equal in value to s but after it in the
+// order is not yet part of the sublevel set at s. One CTA per tile: first the
+// tile's branch minima (s != u), then, after a barrier, its inner vertices
+// (s == u != v), whose chases start at the tile's (now repaired) minima and
+// so mostly hit L1. Concurrent repairs only replace a target by one further
+// along the same chain below the same level, so a stale cached copy of an
+// entry is still a valid (longer) way to the same answer: the chases use
+// ordinary L1-cached loads.
+template <int LX, int LY, int LZ, int NT>
+__global__ void __launch_bounds__(NT) k_repair(uint64_t *W, const float *__restrict__ f, uint32_t nx, uint32_t ny,
+                                               uint32_t nz, uint32_t ntx, uint32_t nty, uint32_t *status)
 {
     if (*status) return;
-    for (uint64_t uu = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; uu < n;
-         uu += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = (uint32_t)uu;
-        const uint64_t T = W[u];
-        const uint32_t s = tri_s(T), t = tri_v(T);
-        if (mode == 0 ? (s == u) : (s != u || t == u)) continue;
-        uint32_t steps = 0;
-        const uint32_t r = representative_cached(W, f, t, s, __ldg(f + s), steps);
-        if (steps > kChaseLimit) {
-            raise_status(status, ST_TIMEOUT);
-            continue;
+    using TS = Tile<LX, LY, LZ>;
+    constexpr uint32_t TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+    const uint32_t wx = min(TX, nx - x0), wy = min(TY, ny - y0), wz = min(TZ, nz - z0);
+    const uint32_t nxy = nx * ny;
+    const uint32_t base = z0 * nxy + y0 * nx + x0;
+    bool ok = true;
+    for (int pass = 0; pass < 2; pass++) {
+        for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+            const uint32_t lx = l & (TX - 1), ly = (l >> LX) & (TY - 1), lz = l >> (LX + LY);
+            if (lx >= wx || ly >= wy || lz >= wz) continue;
+            const uint32_t u = base + lz * nxy + ly * nx + lx;
+            const uint64_t T = W[u];
+            const uint32_t s = tri_s(T), t = tri_v(T);
+            if (pass == 0 ? (s == u) : (s != u || t == u)) continue;
+            uint32_t steps = 0;
+            const uint32_t r = representative_cached(W, f, t, s, __ldg(f + s), steps);
+            if (steps > kChaseLimit) {
+                ok = false;
+                continue;
+            }
+            if (r != t) st_tri(W + u, tri_pack(s, r));
         }
-        if (r != t) st_tri(W + u, tri_pack(s, r));
+        __syncthreads();
     }
+    if (!ok) raise_status(status, ST_TIMEOUT);
 }
 
 // ------------------------------------------------------------ host side
 
-static int grid_for(uint64_t work, int threads)
-{
-    const uint64_t want = (work + threads - 1) / threads;
-    const uint64_t cap = (uint64_t)device_sms() * 8;  // 8 resident 256-thread CTAs per SM
-    return (int)(want < cap ? (want ? want : 1) : cap);
-}
-
 // Tile shape 32 x 16 x 16: 8192 vertices, about 108 KiB of shared memory,
-// two CTAs of 1024 threads per SM; 8 level buckets.
+// two CTAs of 1024 threads per SM; 8 level buckets. (16^3 tiles with four
+// CTAs of 512 threads per SM measured slower: more cross-tile edges.)
 constexpr int kLX = 5, kLY = 4, kLZ = 4, kTileThreads = 1024, kBuckets = 8;
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
                          cudaStream_t st)
 {
-    using TS = Tile<kLX, kLY, kLZ>;
-    const uint64_t n = (uint64_t)nx * ny * nz;
+    using TS = Tile<kLX, kLY, kLZ, kTileThreads>;
     const int vec = (nx % 4 == 0) && ((uintptr_t)f % 16 == 0) && ((uintptr_t)W % 16 == 0);
     const uint32_t ntx = (nx + TS::TX - 1) / TS::TX, nty = (ny + TS::TY - 1) / TS::TY,
                    ntz = (nz + TS::TZ - 1) / TS::TZ;
@@ -542,10 +549,8 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     PhaseScope ps(kRepair, st);
-    k_repair<<<grid_for(n, 256), 256, 0, st>>>(W, f, n, 0, ws.status);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_repair<<<grid_for(n, 256), 256, 0, st>>>(W, f, n, 1, ws.status);
-    count_launch(2);
+    k_repair<kLX, kLY, kLZ, 512><<<(unsigned)ntiles, 512, 0, st>>>(W, f, nx, ny, nz, ntx, nty, ws.status);
+    count_launch();
     return cudaGetLastError();
 }
 

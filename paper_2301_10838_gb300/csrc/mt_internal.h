@@ -44,7 +44,7 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
                          cudaStream_t st);
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
                          cudaStream_t st);
-cudaError_t launch_labels(const float *f, const uint64_t *W, uint64_t n, float t, uint32_t *labels, Workspace &ws,
-                          cudaStream_t st);
+cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, float t,
+                          uint32_t *labels, Workspace &ws, cudaStream_t st);
 
 }  // namespace mt

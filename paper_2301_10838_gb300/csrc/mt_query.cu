@@ -141,15 +141,28 @@ cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_
 // the paper's Representative uses), the deepest vertex of u's component, or
 // 0xFFFFFFFF when f[u] > t. An inner vertex u with f[u] <= t hops to its
 // deepest vertex v first (its link's saddle is u itself), then the chain of
-// branch links is followed while their saddles lie in G_t.
-__global__ void __launch_bounds__(256) k_labels(const float *__restrict__ f, const uint64_t *__restrict__ W,
-                                                uint64_t n, float t, uint32_t *__restrict__ labels,
-                                                uint32_t *status)
+// branch links is followed while their saddles lie in G_t. The vertices are
+// visited brick by brick (32 x 16 x 16, one CTA each) so that the many
+// vertices sharing a representative find its chain in L1.
+constexpr uint32_t kLabLX = 5, kLabLY = 4, kLabLZ = 4;
+
+__global__ void __launch_bounds__(512) k_labels(const float *__restrict__ f, const uint64_t *__restrict__ W,
+                                                uint32_t nx, uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty,
+                                                float t, uint32_t *__restrict__ labels, uint32_t *status)
 {
     if (*status) return;
-    for (uint64_t uu = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; uu < n;
-         uu += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = (uint32_t)uu;
+    constexpr uint32_t TX = 1u << kLabLX, TY = 1u << kLabLY, TZ = 1u << kLabLZ, TV = TX * TY * TZ;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+    const uint32_t wx = min(TX, nx - x0), wy = min(TY, ny - y0), wz = min(TZ, nz - z0);
+    const uint32_t nxy = nx * ny;
+    const uint32_t base = z0 * nxy + y0 * nx + x0;
+    bool ok = true;
+    for (uint32_t l = threadIdx.x; l < TV; l += blockDim.x) {
+        const uint32_t lx = l & (TX - 1), ly = (l >> kLabLX) & (TY - 1), lz = l >> (kLabLX + kLabLY);
+        if (lx >= wx || ly >= wy || lz >= wz) continue;
+        const uint32_t u = base + lz * nxy + ly * nx + lx;
         uint32_t lab = 0xFFFFFFFFu;
         if (__ldg(f + u) <= t) {
             uint32_t x = u;
@@ -159,23 +172,24 @@ __global__ void __launch_bounds__(256) k_labels(const float *__restrict__ f, con
                 if (T == tri_pack(x, x) || !(__ldg(f + s) <= t)) break;
                 x = tri_v(T);
                 if (h > kChaseLimit) {
-                    raise_status(status, ST_TIMEOUT);
+                    ok = false;
                     break;
                 }
             }
             lab = x;
         }
-        labels[uu] = lab;
+        labels[u] = lab;
     }
+    if (!ok) raise_status(status, ST_TIMEOUT);
 }
 
-cudaError_t launch_labels(const float *f, const uint64_t *W, uint64_t n, float t, uint32_t *labels, Workspace &ws,
-                          cudaStream_t st)
+cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, float t,
+                          uint32_t *labels, Workspace &ws, cudaStream_t st)
 {
     PhaseScope ps(kLabels, st);
     count_launch();
-    const uint64_t want = (n + 255) / 256, cap = (uint64_t)device_sms() * 8;
-    k_labels<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(f, W, n, t, labels, ws.status);
+    const uint32_t ntx = (nx + 31) >> kLabLX, nty = (ny + 15) >> kLabLY, ntz = (nz + 15) >> kLabLZ;
+    k_labels<<<ntx * nty * ntz, 512, 0, st>>>(f, W, nx, ny, nz, ntx, nty, t, labels, ws.status);
     return cudaGetLastError();
 }
 
