@@ -119,6 +119,51 @@ mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, flo
  */
 mt_status mt_sync_status(void *d_ws, void *stream);
 
+/* ------------------------------------------------------------- batches
+ * Many fields of uneven sizes in one pass (not in the paper: a batched mode
+ * built on the same kernels). Field i occupies elements [off_i, off_i + n_i)
+ * of the field arena and of the triplet arena, off_i = n_0 + ... + n_{i-1};
+ * its pairs go to pair slots [off_i, off_i + n_i) of the pair arena
+ * (uint32[sum n][2]), so every field has room for all its pairs. Vertex ids in
+ * triplets and pairs are local to their field. d_npairs[i] receives field
+ * i's number of pairs. The results equal those of the single-field calls on
+ * each field.
+ */
+typedef struct {
+    uint32_t nfields;
+    uint32_t tiles[2];      /* tiles of the two tile shapes */
+    uint64_t chunks;        /* pair-compaction chunks */
+    uint64_t vertices;      /* sum of n_i */
+    uint64_t ws_bytes;      /* workspace the plan needs */
+} mt_batch_plan;
+
+/* Workspace for a batch (0 if any grid is invalid); 256-byte aligned. */
+size_t mt_batch_workspace_bytes(const mt_grid *h_grids, uint32_t nfields);
+
+/* Validates the grids, writes the field table (arena pointers, offsets,
+ * tilings) into the workspace and fills *plan. Synchronises `stream`. Call it
+ * again whenever the arenas or the grids change. */
+mt_status mt_batch_prepare(const float *d_arena, const mt_grid *h_grids, uint32_t nfields, uint64_t *d_W_arena,
+                           uint32_t *d_pairs_arena, void *d_ws, size_t ws_bytes, mt_batch_plan *plan, void *stream);
+
+/* Enqueues the batched build and pair compaction on `stream`: memsets and
+ * kernel launches only, nothing synchronises, so it may be captured in a
+ * CUDA graph. variant 0 uses 32x16x16 tiles, 1 uses 16x16x8 tiles (both give
+ * the same results). Device errors land in the workspace status word
+ * (mt_sync_status). */
+mt_status mt_batch_launch(const mt_batch_plan *plan, int variant, uint64_t *d_npairs, void *d_ws, size_t ws_bytes,
+                          void *stream);
+
+/* mt_batch_prepare followed by mt_batch_launch with variant 0. */
+mt_status mt_batch_build(const float *d_arena, const mt_grid *h_grids, uint32_t nfields, uint64_t *d_W_arena,
+                         uint32_t *d_pairs_arena, uint64_t *d_npairs, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Autotuner: runs each tile variant once to warm up and three times timed
+ * (CUDA events on `stream`), writes the best times to ms[0..1] and the faster
+ * variant to *best. Synchronises. */
+mt_status mt_batch_autotune(const mt_batch_plan *plan, uint64_t *d_npairs, void *d_ws, size_t ws_bytes, void *stream,
+                            float *ms, int *best);
+
 /*
  * Persistence pairs for callers that cannot allocate device memory. The paper
  * has no counterpart to this call; it exists because some callers may not

@@ -7,10 +7,16 @@ load libmt; the first ``mt_*`` call does, and raises if it is not built.
 """
 
 from .binding import (  # noqa: F401
+    BatchPlan,
     Grid,
     MtError,
     grid_of,
     load,
+    mt_batch_autotune,
+    mt_batch_build,
+    mt_batch_launch,
+    mt_batch_prepare,
+    mt_batch_workspace_bytes,
     mt_build_triplets,
     mt_components_at,
     mt_persistence_pairs,
@@ -25,7 +31,13 @@ from .binding import (  # noqa: F401
 )
 
 __all__ = [
+    "BatchPlan",
     "Grid",
+    "mt_batch_autotune",
+    "mt_batch_build",
+    "mt_batch_launch",
+    "mt_batch_prepare",
+    "mt_batch_workspace_bytes",
     "MtError",
     "grid_of",
     "load",

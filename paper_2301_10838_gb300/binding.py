@@ -34,6 +34,12 @@ __all__ = [
     "mt_components_at",
     "mt_sync_status",
     "mt_persistence_pairs_noalloc",
+    "BatchPlan",
+    "mt_batch_workspace_bytes",
+    "mt_batch_prepare",
+    "mt_batch_launch",
+    "mt_batch_build",
+    "mt_batch_autotune",
     "mt_trace_enable",
     "mt_trace_read",
     "mt_kernel_launches",
@@ -57,6 +63,11 @@ class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_uint32), ("ny", ctypes.c_uint32), ("nz", ctypes.c_uint32)]
 
 
+class BatchPlan(ctypes.Structure):
+    _fields_ = [("nfields", ctypes.c_uint32), ("tiles", ctypes.c_uint32 * 2), ("chunks", ctypes.c_uint64),
+                ("vertices", ctypes.c_uint64), ("ws_bytes", ctypes.c_uint64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -70,6 +81,11 @@ _SIGS = {
     "mt_components_at": ([_P, _P, Grid, ctypes.c_float, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_sync_status": ([_P, _P], ctypes.c_int32),
     "mt_persistence_pairs_noalloc": ([_P, _P, Grid, _P, _U64, _P, _P, _P], ctypes.c_int32),
+    "mt_batch_workspace_bytes": ([_P, ctypes.c_uint32], ctypes.c_size_t),
+    "mt_batch_prepare": ([_P, _P, ctypes.c_uint32, _P, _P, _P, ctypes.c_size_t, _P, _P], ctypes.c_int32),
+    "mt_batch_launch": ([_P, ctypes.c_int, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
+    "mt_batch_build": ([_P, _P, ctypes.c_uint32, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
+    "mt_batch_autotune": ([_P, _P, _P, ctypes.c_size_t, _P, _P, _P], ctypes.c_int32),
     "mt_trace_enable": ([ctypes.c_int], None),
     "mt_trace_read": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "mt_kernel_launches": ([], ctypes.c_ulonglong),
@@ -204,6 +220,62 @@ def mt_persistence_pairs_noalloc(f: torch.Tensor, W: torch.Tensor, pairs: torch.
         return int(npairs.value), int(root.value)
     _check(code, "mt_persistence_pairs_noalloc", f" npairs={npairs.value} cap={cap}")
     return int(npairs.value), int(root.value)
+
+
+def _grid_array(grids):
+    arr = (Grid * len(grids))()
+    for i, g in enumerate(grids):
+        arr[i] = g if isinstance(g, Grid) else Grid(*g)
+    return arr
+
+
+def mt_batch_workspace_bytes(grids) -> int:
+    arr = _grid_array(grids)
+    return int(load().mt_batch_workspace_bytes(ctypes.cast(arr, ctypes.c_void_p), len(grids)))
+
+
+def mt_batch_prepare(arena: torch.Tensor, grids, W_arena: torch.Tensor, pairs_arena: torch.Tensor,
+                     ws: torch.Tensor, stream=None) -> BatchPlan:
+    """Writes the batch's field table into ``ws``; returns the plan. ``grids``
+    are Grid(nx, ny, nz) (or (nx, ny, nz) tuples) in arena order."""
+    arr = _grid_array(grids)
+    total = sum(g.nx * g.ny * g.nz for g in arr)
+    pa = _dev(arena, "arena", (torch.float32,), total)
+    pW = _dev(W_arena, "W_arena", _I64, total)
+    pp = _dev(pairs_arena, "pairs_arena", _I32, 2 * total)
+    pws = _dev(ws, "ws", (torch.uint8,))
+    plan = BatchPlan()
+    _check(load().mt_batch_prepare(pa, ctypes.cast(arr, ctypes.c_void_p), len(grids), pW, pp, pws, ws.numel(),
+                                   ctypes.byref(plan), _stream_ptr(stream)), "mt_batch_prepare")
+    return plan
+
+
+def mt_batch_launch(plan: BatchPlan, variant: int, npairs: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    pn = _dev(npairs, "npairs", _I64, plan.nfields)
+    pws = _dev(ws, "ws", (torch.uint8,))
+    _check(load().mt_batch_launch(ctypes.byref(plan), int(variant), pn, pws, ws.numel(), _stream_ptr(stream)),
+           "mt_batch_launch")
+
+
+def mt_batch_build(arena: torch.Tensor, grids, W_arena: torch.Tensor, pairs_arena: torch.Tensor,
+                   npairs: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    arr = _grid_array(grids)
+    total = sum(g.nx * g.ny * g.nz for g in arr)
+    _check(load().mt_batch_build(_dev(arena, "arena", (torch.float32,), total), ctypes.cast(arr, ctypes.c_void_p),
+                                 len(grids), _dev(W_arena, "W_arena", _I64, total),
+                                 _dev(pairs_arena, "pairs_arena", _I32, 2 * total),
+                                 _dev(npairs, "npairs", _I64, len(grids)), _dev(ws, "ws", (torch.uint8,)),
+                                 ws.numel(), _stream_ptr(stream)), "mt_batch_build")
+
+
+def mt_batch_autotune(plan: BatchPlan, npairs: torch.Tensor, ws: torch.Tensor, stream=None):
+    """Times both tile variants; returns ([ms0, ms1], best)."""
+    ms = (ctypes.c_float * 2)()
+    best = ctypes.c_int(0)
+    _check(load().mt_batch_autotune(ctypes.byref(plan), _dev(npairs, "npairs", _I64, plan.nfields),
+                                    _dev(ws, "ws", (torch.uint8,)), ws.numel(), _stream_ptr(stream),
+                                    ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(best)), "mt_batch_autotune")
+    return [float(ms[0]), float(ms[1])], int(best.value)
 
 
 def mt_components_at(f: torch.Tensor, W: torch.Tensor, t: float, labels: torch.Tensor, ws: torch.Tensor,

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "mt_device.cuh"
+#include "mt_fields.cuh"
 #include "mt_internal.h"
 
 namespace mt {
@@ -138,10 +139,12 @@ __device__ __forceinline__ void sm_merge(uint32_t *T, const uint32_t *K, uint32_
 }
 
 template <int LX, int LY, int LZ, int NT, int NB>
-__global__ void __launch_bounds__(NT, 2048 / NT) k_tile(const float *__restrict__ f, uint64_t *__restrict__ W, uint32_t nx,
-                                                uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty, int vec,
-                                                uint32_t *status)
+__device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, uint32_t *status)
 {
+    const float *__restrict__ f = fd.f;
+    uint64_t *__restrict__ W = fd.W;
+    const uint32_t nx = fd.nx, ny = fd.ny, nz = fd.nz, ntx = fd.ntx, nty = fd.nty;
+    const bool vec = (nx % 4 == 0) && ((uintptr_t)f % 16 == 0) && ((uintptr_t)W % 16 == 0);
     using TS = Tile<LX, LY, LZ, NT>;
     constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV, BINS = TS::kBins, Q = TS::kQueue;
     constexpr uint32_t IDB = LX + LY + LZ;  // bits of a local id
@@ -160,7 +163,6 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_tile(const float *__restrict_
     __shared__ uint32_t s_boff[NB + 1], s_bcur[NB];
 
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t tile = blockIdx.x;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
     const uint32_t wx = min((uint32_t)TX, nx - x0), wy = min((uint32_t)TY, ny - y0),
@@ -416,6 +418,32 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_tile(const float *__restrict_
     }
 }
 
+// One CTA per tile (queue == null), or a persistent grid that takes tiles
+// from a device-side counter until none is left (the batched build).
+template <int LX, int LY, int LZ, int NT, int NB, class Loc>
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 2 : 1536 / NT) k_tile(Loc loc, uint32_t ntiles, uint32_t *queue,
+                                                                      uint32_t *status)
+{
+    if (queue == nullptr) {
+        uint32_t local;
+        const FieldDesc fd = loc.tile(blockIdx.x, local);
+        tile_body<LX, LY, LZ, NT, NB>(fd, local, status);
+        return;
+    }
+    __shared__ uint32_t s_next;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t t = s_next;
+        __syncthreads();
+        if (t >= ntiles) break;
+        uint32_t local;
+        const FieldDesc fd = loc.tile(t, local);
+        tile_body<LX, LY, LZ, NT, NB>(fd, local, status);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- k_cross
 //
 // The rest of the edge loop of Algorithm 1: the edges between neighbouring
@@ -424,14 +452,17 @@ __global__ void __launch_bounds__(NT, 2048 / NT) k_tile(const float *__restrict_
 // the climbs of one CTA stay mostly within a few tiles' entries (L2 reuse).
 // A merge for edge (a, b) at level S = the later of a, b starts at a and b
 // themselves; their tile triplets lead to the tile-local deepest vertices.
-template <int LX, int LY, int LZ>
-__global__ void __launch_bounds__(256) k_cross(uint64_t *W, const float *__restrict__ f, uint32_t nx, uint32_t ny,
-                                               uint32_t nz, uint32_t ntx, uint32_t nty, uint32_t *status)
+template <int LX, int LY, int LZ, class Loc>
+__global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
 {
     if (*status) return;
     using TS = Tile<LX, LY, LZ>;
     constexpr uint32_t TX = TS::TX, TY = TS::TY, TZ = TS::TZ;
-    const uint32_t tile = blockIdx.x;
+    uint32_t tile;
+    const FieldDesc fd = loc.tile(blockIdx.x, tile);
+    uint64_t *W = fd.W;
+    const float *__restrict__ f = fd.f;
+    const uint32_t nx = fd.nx, ny = fd.ny, nz = fd.nz, ntx = fd.ntx, nty = fd.nty;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
     const uint32_t wx = min(TX, nx - x0), wy = min(TY, ny - y0), wz = min(TZ, nz - z0);
@@ -473,14 +504,17 @@ __global__ void __launch_bounds__(256) k_cross(uint64_t *W, const float *__restr
 // along the same chain below the same level, so a stale cached copy of an
 // entry is still a valid (longer) way to the same answer: the chases use
 // ordinary L1-cached loads.
-template <int LX, int LY, int LZ, int NT>
-__global__ void __launch_bounds__(NT) k_repair(uint64_t *W, const float *__restrict__ f, uint32_t nx, uint32_t ny,
-                                               uint32_t nz, uint32_t ntx, uint32_t nty, uint32_t *status)
+template <int LX, int LY, int LZ, int NT, class Loc>
+__global__ void __launch_bounds__(NT) k_repair(Loc loc, uint32_t *status)
 {
     if (*status) return;
     using TS = Tile<LX, LY, LZ>;
     constexpr uint32_t TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV;
-    const uint32_t tile = blockIdx.x;
+    uint32_t tile;
+    const FieldDesc fd = loc.tile(blockIdx.x, tile);
+    uint64_t *W = fd.W;
+    const float *__restrict__ f = fd.f;
+    const uint32_t nx = fd.nx, ny = fd.ny, nz = fd.nz, ntx = fd.ntx, nty = fd.nty;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
     const uint32_t wx = min(TX, nx - x0), wy = min(TY, ny - y0), wz = min(TZ, nz - z0);
@@ -510,48 +544,91 @@ __global__ void __launch_bounds__(NT) k_repair(uint64_t *W, const float *__restr
 
 // ------------------------------------------------------------ host side
 
-// Tile shape 32 x 16 x 16: 8192 vertices, about 108 KiB of shared memory,
-// two CTAs of 1024 threads per SM; 8 level buckets. (16^3 tiles with four
-// CTAs of 512 threads per SM measured slower: more cross-tile edges.)
-constexpr int kLX = 5, kLY = 4, kLZ = 4, kTileThreads = 1024, kBuckets = 8;
+// Tile shapes. Variant 0: 32 x 16 x 16, 8192 vertices, about 108 KiB of
+// shared memory, two CTAs of 1024 threads per SM (16^3 tiles with four CTAs
+// of 512 threads measured slower on the 1024^3 field: more cross-tile edges).
+// Variant 1: 16 x 16 x 8, 2048 vertices, about 26 KiB, six CTAs of 256
+// threads per SM, for batches of small fields that would leave most of a
+// large tile empty. 8 level buckets in both.
+constexpr int kBuckets = 8;
+template <int V> struct Variant;
+template <> struct Variant<0> { static constexpr int LX = 5, LY = 4, LZ = 4, NT = 1024; };
+template <> struct Variant<1> { static constexpr int LX = 4, LY = 4, LZ = 3, NT = 256; };
 
-cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         cudaStream_t st)
+void tile_shape(int variant, uint32_t &tx, uint32_t &ty, uint32_t &tz)
 {
-    using TS = Tile<kLX, kLY, kLZ, kTileThreads>;
-    const int vec = (nx % 4 == 0) && ((uintptr_t)f % 16 == 0) && ((uintptr_t)W % 16 == 0);
-    const uint32_t ntx = (nx + TS::TX - 1) / TS::TX, nty = (ny + TS::TY - 1) / TS::TY,
-                   ntz = (nz + TS::TZ - 1) / TS::TZ;
-    const uint64_t ntiles = (uint64_t)ntx * nty * ntz;
+    if (variant == 1) {
+        tx = 1u << Variant<1>::LX, ty = 1u << Variant<1>::LY, tz = 1u << Variant<1>::LZ;
+    } else {
+        tx = 1u << Variant<0>::LX, ty = 1u << Variant<0>::LY, tz = 1u << Variant<0>::LZ;
+    }
+}
+
+template <int V, class Loc>
+static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, int persistent_grid, uint32_t *status,
+                             cudaStream_t st)
+{
+    using VV = Variant<V>;
+    using TS = Tile<VV::LX, VV::LY, VV::LZ, VV::NT>;
+    auto ktile = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, Loc>;
     const size_t smem = TS::kSmem;
+    static bool attr_done = false;  // per instantiation
     cudaError_t e;
-    static bool attr_done = false;
     if (!attr_done) {
-        e = cudaFuncSetAttribute(k_tile<kLX, kLY, kLZ, kTileThreads, kBuckets>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_tile<kLX, kLY, kLZ, kTileThreads, kBuckets>,
-                                 cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(ktile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(ktile, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+            return e;
         attr_done = true;
     }
     {
         PhaseScope ps(kTile, st);
-        k_tile<kLX, kLY, kLZ, kTileThreads, kBuckets><<<(unsigned)ntiles, kTileThreads, smem, st>>>(f, W, nx, ny, nz, ntx,
-                                                                                         nty, vec, ws.status);
+        const unsigned grid = queue ? (unsigned)persistent_grid : ntiles;
+        ktile<<<grid, VV::NT, smem, st>>>(loc, ntiles, queue, status);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
         PhaseScope ps(kMerge, st);
-        k_cross<kLX, kLY, kLZ><<<(unsigned)ntiles, 256, 0, st>>>(W, f, nx, ny, nz, ntx, nty, ws.status);
+        k_cross<VV::LX, VV::LY, VV::LZ, Loc><<<ntiles, 256, 0, st>>>(loc, status);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     PhaseScope ps(kRepair, st);
-    k_repair<kLX, kLY, kLZ, 512><<<(unsigned)ntiles, 512, 0, st>>>(W, f, nx, ny, nz, ntx, nty, ws.status);
+    k_repair<VV::LX, VV::LY, VV::LZ, 512, Loc><<<ntiles, 512, 0, st>>>(loc, status);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
+                         cudaStream_t st)
+{
+    using VV = Variant<0>;
+    OneField loc;
+    loc.d = FieldDesc{};
+    loc.d.f = f;
+    loc.d.W = W;
+    loc.d.nx = nx, loc.d.ny = ny, loc.d.nz = nz;
+    loc.d.n = (uint64_t)nx * ny * nz;
+    loc.d.ntx = (nx + (1u << VV::LX) - 1) >> VV::LX;
+    loc.d.nty = (ny + (1u << VV::LY) - 1) >> VV::LY;
+    const uint32_t ntz = (nz + (1u << VV::LZ) - 1) >> VV::LZ;
+    const uint64_t ntiles = (uint64_t)loc.d.ntx * loc.d.nty * ntz;
+    return run_build<0>(loc, (uint32_t)ntiles, nullptr, 0, ws.status, st);
+}
+
+cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint32_t ntiles, int variant,
+                               uint32_t *status, uint32_t *queue, cudaStream_t st)
+{
+    ManyFields loc{d_descs, nfields};
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    // persistent grid: as many CTAs as fit on the GPU at once
+    const int per_sm = variant == 1 ? 1536 / Variant<1>::NT : 2;
+    const int grid = device_sms() * per_sm;
+    if (variant == 1) return run_build<1>(loc, ntiles, queue, grid, status, st);
+    return run_build<0>(loc, ntiles, queue, grid, status, st);
 }
 
 }  // namespace mt

@@ -10,6 +10,21 @@ namespace mt {
 // Vertices per block of the ordered compactions (pairs): 256 threads x 16.
 constexpr uint32_t kCompactChunk = 4096;
 
+// One field as the kernels see it. In a batch, fields are packed one after
+// another in the field, triplet and pair arenas, and tile0 / chunk0 number
+// each field's first tile and first compaction chunk across the batch.
+struct FieldDesc {
+    const float *f;    // values, [nz][ny][nx]
+    uint64_t *W;       // triplets, field-local vertex ids
+    uint32_t *pairs;   // pair output ([cap][2]) or null
+    uint64_t *meta;    // [0] npairs, [1] number of roots, [2] root
+    uint64_t n, cap;   // vertices, pair capacity
+    uint64_t chunk0;   // first compaction chunk of the field
+    uint32_t nx, ny, nz;
+    uint32_t ntx, nty; // tiles along x and y for the tile shape in use
+    uint32_t tile0;    // first tile of the field
+};
+
 // Views into the caller's workspace (layout fixed by carve_workspace).
 struct Workspace {
     uint32_t *status;  // status bits (ST_*)
@@ -44,6 +59,14 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
                          cudaStream_t st);
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
                          cudaStream_t st);
+
+// Batched build and pairs over a packed descriptor table already in device
+// memory; variant selects the tile shape (mt_build.cu, mt_query.cu).
+cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint32_t ntiles, int variant,
+                               uint32_t *status, uint32_t *queue, cudaStream_t st);
+cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint64_t nchunks, uint32_t *counts,
+                               uint64_t *npairs, const uint32_t *status, cudaStream_t st);
+void tile_shape(int variant, uint32_t &tx, uint32_t &ty, uint32_t &tz);
 cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, float t,
                           uint32_t *labels, Workspace &ws, cudaStream_t st);
 

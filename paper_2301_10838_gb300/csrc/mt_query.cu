@@ -7,28 +7,33 @@
 #include <cuda_runtime.h>
 
 #include "mt_device.cuh"
+#include "mt_fields.cuh"
 #include "mt_internal.h"
 
 namespace mt {
 
 // ------------------------------------------------------------------ pairs
 //
-// One CTA per chunk of kCompactChunk consecutive vertices, read in 16 rounds
-// of 256 consecutive vertices so that every load is coalesced. A pass counts
-// the pairs of each chunk (and finds the roots), a single-CTA scan turns the
-// counts into offsets, and a second pass writes each chunk's pairs at its
-// offset in order. Each round ranks its flags with warp ballots plus a
+// One CTA per chunk of kCompactChunk consecutive vertices of a field, read in
+// 16 rounds of 256 consecutive vertices so that every load is coalesced. A
+// pass counts the pairs of each chunk (and finds the roots), a scan per field
+// turns the counts into offsets, and a second pass writes each chunk's pairs
+// at its offset in order. Each round ranks its flags with warp ballots plus a
 // prefix over the 8 warp totals, which keeps the ascending order.
 constexpr int kCompactThreads = 256;
 constexpr int kCompactRounds = kCompactChunk / kCompactThreads;
 
-__global__ void __launch_bounds__(kCompactThreads) k_pairs_count(const uint64_t *__restrict__ W, uint64_t n,
-                                                                 uint32_t *counts, uint64_t *meta,
-                                                                 const uint32_t *status)
+template <class Loc>
+__global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32_t *counts, const uint32_t *status)
 {
     if (*status) return;
     __shared__ uint32_t warp_sum[kCompactThreads / 32];
-    const uint64_t b0 = (uint64_t)blockIdx.x * kCompactChunk;
+    uint64_t local;
+    uint32_t fi;
+    const FieldDesc fd = loc.chunk(blockIdx.x, local, fi);
+    const uint64_t *__restrict__ W = fd.W;
+    const uint64_t n = fd.n;
+    const uint64_t b0 = local * kCompactChunk;
     uint32_t c = 0;
     for (int r = 0; r < kCompactRounds; r++) {
         const uint64_t u = b0 + (uint64_t)r * kCompactThreads + threadIdx.x;
@@ -37,8 +42,8 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(const uint64_t 
         if (tri_s(T) != (uint32_t)u) {
             c++;
         } else if (tri_v(T) == (uint32_t)u) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(meta + 1), 1ull);
-            meta[2] = u;
+            atomicAdd(reinterpret_cast<unsigned long long *>(fd.meta + 1), 1ull);
+            fd.meta[2] = u;
         }
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -51,17 +56,22 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(const uint64_t 
     }
 }
 
-// Exclusive scan of counts[0..m) in place by one CTA of 1024 threads; the
-// total goes to meta[0].
-__global__ void __launch_bounds__(1024) k_scan_counts(uint32_t *counts, uint64_t m, uint64_t *meta,
+// Exclusive scan of one field's chunk counts in place (one CTA of 1024
+// threads per field); the field's total goes to its meta[0] and, in a batch,
+// to npairs[field].
+template <class Loc>
+__global__ void __launch_bounds__(1024) k_scan_counts(Loc loc, uint32_t *counts, uint64_t *npairs,
                                                       const uint32_t *status)
 {
     if (*status) return;
     __shared__ uint64_t part[1024];
+    const FieldDesc fd = loc.field(blockIdx.x);
+    uint32_t *cnt = counts + fd.chunk0;
+    const uint64_t m = (fd.n + kCompactChunk - 1) / kCompactChunk;
     const uint64_t per = (m + 1023) / 1024;
     const uint64_t a = threadIdx.x * per, b = a + per < m ? a + per : m;
     uint64_t s = 0;
-    for (uint64_t i = a; i < b; i++) s += counts[i];
+    for (uint64_t i = a; i < b; i++) s += cnt[i];
     part[threadIdx.x] = s;
     __syncthreads();
     // Hillis-Steele inclusive scan of the 1024 partial sums
@@ -73,20 +83,29 @@ __global__ void __launch_bounds__(1024) k_scan_counts(uint32_t *counts, uint64_t
     }
     uint64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
     for (uint64_t i = a; i < b; i++) {
-        const uint32_t c = counts[i];
-        counts[i] = (uint32_t)run;
+        const uint32_t c = cnt[i];
+        cnt[i] = (uint32_t)run;
         run += c;
     }
-    if (threadIdx.x == 1023) meta[0] = part[1023];
+    if (threadIdx.x == 1023) {
+        fd.meta[0] = part[1023];
+        if (npairs) npairs[blockIdx.x] = part[1023];
+    }
 }
 
-__global__ void __launch_bounds__(kCompactThreads) k_pairs_write(const uint64_t *__restrict__ W, uint64_t n,
-                                                                 const uint32_t *offsets, uint32_t *pairs,
-                                                                 uint64_t cap, const uint32_t *status)
+template <class Loc>
+__global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const uint32_t *offsets,
+                                                                 const uint32_t *status)
 {
     if (*status) return;
     __shared__ uint32_t warp_cnt[kCompactThreads / 32];
-    const uint64_t b0 = (uint64_t)blockIdx.x * kCompactChunk;
+    uint64_t local;
+    uint32_t fi;
+    const FieldDesc fd = loc.chunk(blockIdx.x, local, fi);
+    const uint64_t *__restrict__ W = fd.W;
+    const uint64_t n = fd.n, cap = fd.cap;
+    uint32_t *pairs = fd.pairs;
+    const uint64_t b0 = local * kCompactChunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t run = offsets[blockIdx.x];
     for (int r = 0; r < kCompactRounds; r++) {
@@ -119,19 +138,41 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(const uint64_t 
     }
 }
 
+template <class Loc>
+static cudaError_t run_pairs(const Loc &loc, uint32_t nfields, uint64_t nchunks, uint32_t *counts, uint64_t *npairs,
+                             const uint32_t *status, cudaStream_t st)
+{
+    PhaseScope ps(kPairs, st);
+    count_launch(3);
+    k_pairs_count<Loc><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_scan_counts<Loc><<<nfields, 1024, 0, st>>>(loc, counts, npairs, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_pairs_write<Loc><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
                          cudaStream_t st)
 {
-    PhaseScope ps(kPairs, st);
     cudaError_t e = cudaMemsetAsync(ws.meta, 0, 3 * sizeof(uint64_t), st);
     if (e != cudaSuccess) return e;
-    count_launch(3);
-    k_pairs_count<<<(unsigned)ws.nchunks, kCompactThreads, 0, st>>>(W, n, ws.counts, ws.meta, ws.status);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_scan_counts<<<1, 1024, 0, st>>>(ws.counts, ws.nchunks, ws.meta, ws.status);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_pairs_write<<<(unsigned)ws.nchunks, kCompactThreads, 0, st>>>(W, n, ws.counts, pairs, cap, ws.status);
-    return cudaGetLastError();
+    OneField loc;
+    loc.d = FieldDesc{};
+    loc.d.W = const_cast<uint64_t *>(W);
+    loc.d.pairs = pairs;
+    loc.d.meta = ws.meta;
+    loc.d.n = n;
+    loc.d.cap = cap;
+    return run_pairs(loc, 1, ws.nchunks, ws.counts, nullptr, ws.status, st);
+}
+
+cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint64_t nchunks, uint32_t *counts,
+                               uint64_t *npairs, const uint32_t *status, cudaStream_t st)
+{
+    ManyFields loc{d_descs, nfields};
+    return run_pairs(loc, nfields, nchunks, counts, npairs, status, st);
 }
 
 // ----------------------------------------------------------------- labels

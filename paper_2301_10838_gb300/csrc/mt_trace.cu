@@ -65,6 +65,9 @@ void count_launch(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxe
 PhaseScope::PhaseScope(int phase, cudaStream_t st) : phase_(phase), st_(st), a_(nullptr)
 {
     if (!g_on.load(std::memory_order_relaxed)) return;
+    // events recorded into a graph under capture would never be read back
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st_, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> g(g_mu);
     a_ = take_event();
     if (a_) cudaEventRecord(static_cast<cudaEvent_t>(a_), st_);
