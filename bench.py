@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-side", type=int, default=256, help="side of the crop the CPU oracle times")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
 
 
@@ -118,20 +121,26 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ algorithmic bytes
-def algorithmic_bytes(n: int, shape, npairs: int) -> dict:
-    """Bytes the method must move per step (per kernel family):
-      init    read f (4n), write W (8n)
-      merge   two triplet reads per merged edge: 16 E', E' = E - (n - #minima)
+def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 32)) -> dict:
+    """Bytes the method must move per step, by kernel:
+      tile    init: read f (4n) + write W (8n); plus two triplet reads per
+              merged edge inside the tiles, 16 (E' - C)
+      merge   (k_cross) two triplet reads per edge between tiles: 16 C
       repair  read + write W (16n)
       pairs   scan W (8n) + write pairs (8 npairs)
       labels  read f (4n) + W (8n), write labels (4n)
+    E' = E - (n - #minima) (edges that are not steepest-descent seeds, the
+    survey's model) and C the edges between tiles; tile + merge together are
+    the model's 12n + 16E'.
     """
     nz, ny, nx = shape
+    tz, ty, tx = tile
     E = 3 * n - (nx * ny + ny * nz + nz * nx)
     nmin = npairs + 1
     Ep = E - (n - nmin)
-    return {"init": 12 * n, "merge": 16 * Ep, "repair": 16 * n, "pairs": 8 * n + 8 * npairs, "labels": 16 * n,
-            "E": E, "E_prime": Ep}
+    C = ((nx - 1) // tx) * ny * nz + ((ny - 1) // ty) * nx * nz + ((nz - 1) // tz) * nx * ny
+    return {"tile": 12 * n + 16 * (Ep - C), "merge": 16 * C, "repair": 16 * n, "pairs": 8 * n + 8 * npairs,
+            "labels": 16 * n, "E": E, "E_prime": Ep, "cross_edges": C}
 
 
 def measured_peaks():
@@ -234,7 +243,7 @@ def run_ours(args):
                 traffic = json.load(fh).get("dram_bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
-    step_bytes = sum(ab[k] for k in ("init", "merge", "repair", "pairs", "labels"))
+    step_bytes = sum(ab[k] for k in ("tile", "merge", "repair", "pairs", "labels"))
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -280,6 +289,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(f, args.cpu_side)
+    del W, labels, pairs, ws
+    f = None
+    torch.cuda.empty_cache()
+    batch = None if args.no_batch else bench_batch(args, dev)
+    serve = None if args.no_serve else bench_serve(args, dev)
 
     if rank == 0:
         out = {
@@ -316,12 +330,181 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": int(launches),
             "cpu_baseline": cpu,
+            "batch": batch,
+            "serve": serve,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def bench_batch(args, dev):
+    """512 fields of uneven sizes (sides log-uniform in [16, 128] per axis,
+    half white noise, half GRF P(k)~k^-3): one CUDA-graph replay of the
+    batched build + pairs against 512 plain per-field calls on one stream,
+    same outputs."""
+    import numpy as np
+    import torch
+
+    import paper_2301_10838_gb300 as mt
+    from paper_2301_10838_gb300 import fields
+    from paper_2301_10838_gb300.batch import Batch
+
+    shapes = fields.batch_shapes(512, 16, 128, seed=7)
+    flds = [fields.batch_field(i, s) for i, s in enumerate(shapes)]
+    b = Batch(shapes, device=dev)
+    b.load(flds)
+    variant = b.tune()
+    b.capture()
+    st = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        b.launch()
+    torch.cuda.synchronize(dev)
+    reps = max(5, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        b.launch()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    ms_batch = e0.elapsed_time(e1) / reps
+    # plain: one field at a time through the single-field calls
+    ins, outs = [], []
+    for i, s in enumerate(shapes):
+        fi = b.field(i)
+        W = torch.empty(fi.numel(), dtype=torch.int64, device=dev)
+        P = torch.empty((fi.numel(), 2), dtype=torch.int32, device=dev)
+        ws = mt.workspace(mt.grid_of(fi), device=dev)
+        ins.append(fi)
+        outs.append((W, P, ws))
+
+    def plain():
+        ks = []
+        for fi, (W, P, ws) in zip(ins, outs):
+            mt.mt_build_triplets(fi, W, ws)
+            ks.append(mt.mt_persistence_pairs(fi, W, P, ws)[0])
+        return ks
+
+    plain()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    prep = max(2, args.steps // 2)
+    for _ in range(prep):
+        ks = plain()
+    torch.cuda.synchronize(dev)
+    ms_plain = (time.perf_counter() - t0) * 1e3 / prep
+    same = all(int(b.npairs[i]) == ks[i] and torch.equal(b.results(i)[0], outs[i][0]) for i in range(len(shapes)))
+    nv = sum(int(np.prod(s)) for s in shapes)
+    return {"fields": len(shapes), "vertices": nv, "variant": variant,
+            "fields_per_s_batched": round(len(shapes) / (ms_batch / 1e3), 1),
+            "fields_per_s_plain": round(len(shapes) / (ms_plain / 1e3), 1),
+            "ms_per_batch": round(ms_batch, 3), "ms_plain_512": round(ms_plain, 3),
+            "speedup": round(ms_plain / ms_batch, 2), "identical_outputs": bool(same),
+            "timing": "batched: CUDA-graph replays timed with CUDA events; plain: 512 x (mt_build_triplets + "
+                      "mt_persistence_pairs), host wall clock (each pairs call synchronises)"}
+
+
+def bench_serve(args, dev):
+    """Poisson request stream (200 req/s) of GRF fields (P(k)~k^-2.5, unit
+    variance, cubic sides log-uniform in [32, 384]), each asking for pairs and
+    labels at a random threshold; p50/p99 latency from submission to results
+    in host memory. A pool of 24 distinct fields is reused cyclically (each
+    request has its own threshold and output buffers). Also: the same request
+    list submitted at once (saturated throughput) against the plain
+    single-field path run back to back on one stream."""
+    import numpy as np
+    import torch
+
+    import paper_2301_10838_gb300 as mt
+    from paper_2301_10838_gb300 import fields
+    from paper_2301_10838_gb300.serve import Server
+
+    stream = fields.serve_stream(200.0, args.serve_seconds, 32, 384, seed=11)
+    pool_sides = [r.side for r in stream[:24]]
+    pool = []
+    for k, side in enumerate(pool_sides):
+        g = fields.grf((side, side, side), -2.5, 7000 + k, device=str(dev))
+        pool.append(g.cpu().pin_memory())
+        del g
+    torch.cuda.empty_cache()
+    maxn = max(p.numel() for p in pool)
+    R = 48
+    ring = [(torch.empty((maxn // 2 + 1, 2), dtype=torch.int32, pin_memory=True),
+             torch.empty(maxn, dtype=torch.int32, pin_memory=True)) for _ in range(R)]
+    srv = Server(hbm_budget_bytes=24 << 30, max_slots=6, device=dev.index or 0)
+    try:
+        # warm-up
+        for k in range(4):
+            P, L = ring[k]
+            srv.wait(srv.submit(pool[k], 0.0, pairs=P, labels=L))
+        # open-loop Poisson arrivals
+        import threading
+
+        results = [None] * len(stream)
+        tickets = [None] * len(stream)
+        t_start = time.perf_counter()
+
+        def submitter():
+            for i, r in enumerate(stream):
+                delay = t_start + r.arrival_s - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                P, L = ring[i % R]
+                tickets[i] = srv.submit(pool[i % len(pool)], r.threshold, pairs=P, labels=L)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        for i in range(len(stream)):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            results[i] = srv.wait(tickets[i])
+        th.join()
+        wall = time.perf_counter() - t_start
+        lat = np.array([r["latency_s"] for r in results]) * 1e3
+        nvert = sum(pool[i % len(pool)].numel() for i in range(len(stream)))
+        # saturated: every request of the list submitted at once
+        nsat = min(len(stream), 240)
+        t0 = time.perf_counter()
+        tks = []
+        for i in range(nsat):
+            P, L = ring[i % R]
+            tks.append(srv.submit(pool[i % len(pool)], stream[i].threshold, pairs=P, labels=L))
+            if len(tks) > R - 8:  # keep ring buffers unshared
+                srv.wait(tks.pop(0))
+        for tk in tks:
+            srv.wait(tk)
+        sat = nsat / (time.perf_counter() - t0)
+    finally:
+        srv.close()
+    # plain single-field path, back to back on one stream, same work
+    ws_cache = {}
+    t0 = time.perf_counter()
+    nplain = min(len(stream), 120)
+    for i in range(nplain):
+        h = pool[i % len(pool)]
+        fd = h.to(dev, non_blocking=True)
+        n = fd.numel()
+        if n not in ws_cache:
+            ws_cache[n] = (torch.empty(n, dtype=torch.int64, device=dev),
+                           torch.empty((n // 2 + 1, 2), dtype=torch.int32, device=dev),
+                           torch.empty(n, dtype=torch.int32, device=dev), mt.workspace(mt.grid_of(fd), device=dev))
+        W, Pd, Ld, ws = ws_cache[n]
+        mt.mt_build_triplets(fd, W, ws)
+        k, _ = mt.mt_persistence_pairs(fd, W, Pd, ws)
+        mt.mt_components_at(fd, W, stream[i].threshold, Ld, ws)
+        P, L = ring[i % R]
+        P[:k].copy_(Pd[:k])
+        L[:n].copy_(Ld)
+    torch.cuda.synchronize(dev)
+    plain = nplain / (time.perf_counter() - t0)
+    return {"requests": len(stream), "rate_hz": 200.0, "seconds": args.serve_seconds,
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "throughput_req_s": round(len(stream) / wall, 1),
+            "mvertices_s_offered": round(nvert / wall / 1e6, 1),
+            "saturated_fields_per_s": round(sat, 1), "plain_fields_per_s": round(plain, 1),
+            "speedup_saturated_vs_plain": round(sat / plain, 2), "slots": 6, "pool_fields": len(pool)}
 
 
 def cpu_baseline(f_dev, side: int):

@@ -164,6 +164,51 @@ mt_status mt_batch_build(const float *d_arena, const mt_grid *h_grids, uint32_t 
 mt_status mt_batch_autotune(const mt_batch_plan *plan, uint64_t *d_npairs, void *d_ws, size_t ws_bytes, void *stream,
                             float *ms, int *best);
 
+/* ------------------------------------------------------------- serving
+ * A request loop on one GPU (not in the paper). The server owns a device
+ * allocation of hbm_budget_bytes and max_slots CUDA streams. A worker thread
+ * admits submitted requests, in arrival order but skipping those that do not
+ * fit yet, as soon as a slot and enough of the budget are free, so requests
+ * that arrive while others run are started as resources free up and overlap
+ * with them on the device. Each request computes the triplet tree of its
+ * field, its persistence pairs and its labels at threshold t, exactly as the
+ * single-field calls do; the results do not depend on the other requests.
+ * A request needs about 20 bytes of the budget per vertex.
+ */
+typedef struct mt_server mt_server;
+
+typedef struct {
+    mt_status status;  /* MT_OK, or the request's error */
+    uint64_t npairs;   /* number of pairs (also when it exceeded pair_cap) */
+    uint32_t root;     /* root vertex */
+    double t_submit;   /* host steady-clock seconds: submission, */
+    double t_admit;    /* admission to a slot, */
+    double t_done;     /* results in host memory */
+} mt_result;
+
+/* NULL on failure (budget below 1 MiB, max_slots outside 1..64, or the
+ * device allocation failed). */
+mt_server *mt_server_create(size_t hbm_budget_bytes, int max_slots, int device);
+
+/* Queues a request; *ticket identifies it. h_f (float32[n]) is read and
+ * h_pairs (uint32[pair_cap][2], may be NULL) and h_labels (uint32[n], may be
+ * NULL) are written by the server until the request completes: keep them
+ * alive and untouched until then. Pinned host buffers keep the copies
+ * asynchronous; pageable ones work but make the worker wait on each copy.
+ * MT_ERR_NOMEM if the request can never fit the budget. */
+mt_status mt_server_submit(mt_server *srv, const float *h_f, mt_grid g, float t, uint32_t *h_pairs,
+                           uint64_t pair_cap, uint32_t *h_labels, uint64_t *ticket);
+
+/* Non-blocking: MT_OK and *r once the request is done (the result is then
+ * forgotten), MT_ERR_BUSY while it is pending or running. */
+mt_status mt_server_poll(mt_server *srv, uint64_t ticket, mt_result *r);
+
+/* Blocks until the request is done, then as mt_server_poll. */
+mt_status mt_server_wait(mt_server *srv, uint64_t ticket, mt_result *r);
+
+/* Finishes queued and running requests, then frees the server. */
+void mt_server_destroy(mt_server *srv);
+
 /*
  * Persistence pairs for callers that cannot allocate device memory. The paper
  * has no counterpart to this call; it exists because some callers may not

@@ -21,6 +21,11 @@ from .binding import (  # noqa: F401
     mt_components_at,
     mt_persistence_pairs,
     mt_persistence_pairs_noalloc,
+    mt_server_create,
+    mt_server_destroy,
+    mt_server_poll,
+    mt_server_submit,
+    mt_server_wait,
     mt_status_str,
     mt_kernel_launches,
     mt_sync_status,
@@ -45,6 +50,11 @@ __all__ = [
     "mt_components_at",
     "mt_persistence_pairs",
     "mt_persistence_pairs_noalloc",
+    "mt_server_create",
+    "mt_server_destroy",
+    "mt_server_poll",
+    "mt_server_submit",
+    "mt_server_wait",
     "mt_status_str",
     "mt_sync_status",
     "mt_trace_enable",

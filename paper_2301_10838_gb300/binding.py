@@ -40,6 +40,12 @@ __all__ = [
     "mt_batch_launch",
     "mt_batch_build",
     "mt_batch_autotune",
+    "MtResult",
+    "mt_server_create",
+    "mt_server_submit",
+    "mt_server_poll",
+    "mt_server_wait",
+    "mt_server_destroy",
     "mt_trace_enable",
     "mt_trace_read",
     "mt_kernel_launches",
@@ -61,6 +67,11 @@ class MtError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_uint32), ("ny", ctypes.c_uint32), ("nz", ctypes.c_uint32)]
+
+
+class MtResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("npairs", ctypes.c_uint64), ("root", ctypes.c_uint32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 class BatchPlan(ctypes.Structure):
@@ -86,6 +97,11 @@ _SIGS = {
     "mt_batch_launch": ([_P, ctypes.c_int, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_batch_build": ([_P, _P, ctypes.c_uint32, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_batch_autotune": ([_P, _P, _P, ctypes.c_size_t, _P, _P, _P], ctypes.c_int32),
+    "mt_server_create": ([ctypes.c_size_t, ctypes.c_int, ctypes.c_int], _P),
+    "mt_server_submit": ([_P, _P, Grid, ctypes.c_float, _P, _U64, _P, _P], ctypes.c_int32),
+    "mt_server_poll": ([_P, _U64, _P], ctypes.c_int32),
+    "mt_server_wait": ([_P, _U64, _P], ctypes.c_int32),
+    "mt_server_destroy": ([_P], None),
     "mt_trace_enable": ([ctypes.c_int], None),
     "mt_trace_read": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "mt_kernel_launches": ([], ctypes.c_ulonglong),
@@ -276,6 +292,58 @@ def mt_batch_autotune(plan: BatchPlan, npairs: torch.Tensor, ws: torch.Tensor, s
                                     _dev(ws, "ws", (torch.uint8,)), ws.numel(), _stream_ptr(stream),
                                     ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(best)), "mt_batch_autotune")
     return [float(ms[0]), float(ms[1])], int(best.value)
+
+
+def mt_server_create(hbm_budget_bytes: int, max_slots: int, device: int = 0) -> int:
+    h = load().mt_server_create(int(hbm_budget_bytes), int(max_slots), int(device))
+    if not h:
+        raise MtError(-6, "mt_server_create")
+    return h
+
+
+def _host(t: torch.Tensor, name: str, dtypes, numel=None) -> int:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if t.dtype not in dtypes or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous tensor of {dtypes}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} needs at least {numel} elements")
+    return t.data_ptr()
+
+
+def mt_server_submit(srv: int, f: torch.Tensor, t: float, pairs: torch.Tensor | None,
+                     labels: torch.Tensor | None) -> int:
+    """Queues (f, t) on the server; f, pairs ((cap, 2) int32) and labels (n
+    int32) are host tensors the server reads/writes until the ticket is done."""
+    g = Grid(int(f.shape[2]), int(f.shape[1]), int(f.shape[0]))
+    n = f.numel()
+    pf = _host(f, "f", (torch.float32,))
+    pp = _host(pairs, "pairs", _I32) if pairs is not None else 0
+    cap = int(pairs.shape[0]) if pairs is not None else 0
+    pl = _host(labels, "labels", _I32, n) if labels is not None else 0
+    ticket = ctypes.c_uint64(0)
+    _check(load().mt_server_submit(srv, pf, g, float(t), pp, cap, pl, ctypes.byref(ticket)), "mt_server_submit")
+    return int(ticket.value)
+
+
+def mt_server_poll(srv: int, ticket: int):
+    """MtResult once done, None while pending."""
+    r = MtResult()
+    code = load().mt_server_poll(srv, int(ticket), ctypes.byref(r))
+    if code == -8:
+        return None
+    _check(code, "mt_server_poll")
+    return r
+
+
+def mt_server_wait(srv: int, ticket: int) -> MtResult:
+    r = MtResult()
+    _check(load().mt_server_wait(srv, int(ticket), ctypes.byref(r)), "mt_server_wait")
+    return r
+
+
+def mt_server_destroy(srv: int) -> None:
+    load().mt_server_destroy(srv)
 
 
 def mt_components_at(f: torch.Tensor, W: torch.Tensor, t: float, labels: torch.Tensor, ws: torch.Tensor,
