@@ -143,6 +143,23 @@ def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 32)) -> dict:
             "labels": 16 * n, "E": E, "E_prime": Ep, "cross_edges": C}
 
 
+def traffic_record(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None if there is none or the kernel source changed since it was taken."""
+    import hashlib
+
+    prof = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{WORKLOAD}.json")
+    src = os.path.join(ROOT, "paper_2301_10838_gb300", "csrc", "mt_build.cu")
+    try:
+        with open(prof) as fh:
+            rec = json.load(fh)
+        with open(src, "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()[:16]
+    except (OSError, ValueError):
+        return None
+    return rec.get("dram_bytes_per_launch") if rec.get("mt_build_cu_sha256_16") == h else None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -235,14 +252,7 @@ def run_ours(args):
     dom = max((k for k in phases if k in ab), key=lambda k: phases[k][1])
     calls, tot = phases[dom]
     achieved = ab[dom] / (tot / calls / 1e3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", f"traffic_{dom}_{WORKLOAD}.json")
-    if side == 1024 and os.path.exists(prof):
-        try:
-            with open(prof) as fh:
-                traffic = json.load(fh).get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = traffic_record(dom) if side == 1024 else None
     step_bytes = sum(ab[k] for k in ("tile", "merge", "repair", "pairs", "labels"))
 
     # end to end through the public API with pinned host buffers
