@@ -17,10 +17,22 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 //   [0, 256)     status word, round flag
 //   [256, 512)   meta: npairs, number of roots, root
 //   [512, ...)   per-chunk counts of the ordered compaction
+//   then, for a build, the face buffers (face_words(0) u32 per tile)
 size_t workspace_bytes(uint64_t n)
 {
     const uint64_t nchunks = (n + kCompactChunk - 1) / kCompactChunk;
     return 512 + align256(nchunks * sizeof(uint32_t));
+}
+
+size_t build_workspace_bytes(uint32_t nx, uint32_t ny, uint32_t nz)
+{
+    const uint64_t n = (uint64_t)nx * ny * nz;
+    return workspace_bytes(n) + align256(tile_count(0, nx, ny, nz) * face_words(0) * sizeof(uint32_t));
+}
+
+uint32_t *build_faces(void *base, uint64_t n)
+{
+    return reinterpret_cast<uint32_t *>(static_cast<char *>(base) + workspace_bytes(n));
 }
 
 bool carve_workspace(void *base, size_t bytes, uint64_t n, Workspace &ws)
@@ -86,7 +98,7 @@ size_t mt_workspace_bytes(mt_grid g)
 {
     uint64_t n;
     if (grid_n(g, n) != MT_OK) return 0;
-    return workspace_bytes(n);
+    return build_workspace_bytes(g.nx, g.ny, g.nz);
 }
 
 mt_status mt_build_triplets(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, void *stream)
@@ -96,10 +108,11 @@ mt_status mt_build_triplets(const float *d_f, mt_grid g, uint64_t *d_W, void *d_
     if (st != MT_OK) return st;
     if (!d_f || !d_W || ((uintptr_t)d_f & 3) || ((uintptr_t)d_W & 7)) return MT_ERR_INVALID;
     Workspace ws;
-    if (!carve_workspace(d_ws, ws_bytes, n, ws)) return MT_ERR_INVALID;
+    if (ws_bytes < build_workspace_bytes(g.nx, g.ny, g.nz) || !carve_workspace(d_ws, ws_bytes, n, ws))
+        return MT_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(ws.status, 0, 256, s) != cudaSuccess) return MT_ERR_CUDA;
-    if (launch_build(d_f, d_W, g.nx, g.ny, g.nz, ws, s) != cudaSuccess) return MT_ERR_CUDA;
+    if (launch_build(d_f, d_W, g.nx, g.ny, g.nz, ws, build_faces(d_ws, n), s) != cudaSuccess) return MT_ERR_CUDA;
     return MT_OK;
 }
 

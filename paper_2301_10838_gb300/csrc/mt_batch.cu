@@ -26,8 +26,9 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 //   descriptor tables for tile variants 0 and 1 (nfields each)
 //   per-field meta (npairs, number of roots, root)
 //   per-chunk counts of the pair compaction
+//   face buffers of the tiles (sized for the larger of the two variants)
 struct Layout {
-    size_t descs[2], meta, counts, total;
+    size_t descs[2], meta, counts, faces, total;
     uint32_t tiles[2];
     uint64_t chunks, vertices;
 };
@@ -62,6 +63,9 @@ bool layout_of(const mt_grid *g, uint32_t nf, Layout &L)
     off = al256(off + (size_t)nf * 3 * sizeof(uint64_t));
     L.counts = off;
     off = al256(off + (size_t)L.chunks * sizeof(uint32_t));
+    L.faces = off;
+    const uint64_t fw0 = (uint64_t)L.tiles[0] * face_words(0), fw1 = (uint64_t)L.tiles[1] * face_words(1);
+    off = al256(off + (size_t)(fw0 > fw1 ? fw0 : fw1) * sizeof(uint32_t));
     L.total = off;
     return true;
 }
@@ -110,6 +114,7 @@ mt_status mt_batch_prepare(const float *d_arena, const mt_grid *h_grids, uint32_
             d.ntx = (g.nx + tx - 1) / tx;
             d.nty = (g.ny + ty - 1) / ty;
             d.tile0 = tile0;
+            d.faces = reinterpret_cast<uint32_t *>(ws + L.faces) + (size_t)tile0 * face_words(v);
             tile0 += d.ntx * d.nty * ((g.nz + tz - 1) / tz);
             chunk0 += (d.n + kCompactChunk - 1) / kCompactChunk;
             off += d.n;

@@ -400,6 +400,44 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     if (!ok) raise_status(status, ST_TIMEOUT);
     __syncthreads();
 
+    // 6b. for k_cross: the tile-local top of every face vertex at the level
+    //     of its edge into the neighbouring tile, i.e. the deepest vertex of
+    //     its tile component below that level. Levels compare (key, global
+    //     id), since the other end lies outside the tile. Face buffer of a
+    //     tile: +x, +y, +z, then -x, -y, -z faces, each indexed by the two
+    //     in-face coordinates on the full tile extent.
+    if (fd.faces) {
+        constexpr uint32_t FX = TY * TZ, FY = TX * TZ, FZ = TX * TY, FH = FX + FY + FZ;
+        uint32_t *out = fd.faces + (size_t)tile * (2 * FH);
+        const uint32_t has_n = (uint32_t)(x0 + TX < nx) | (uint32_t)(y0 + TY < ny) << 1 |
+                               (uint32_t)(z0 + TZ < nz) << 2 | (uint32_t)(x0 > 0) << 3 | (uint32_t)(y0 > 0) << 4 |
+                               (uint32_t)(z0 > 0) << 5;
+        for (uint32_t e = threadIdx.x; e < 2 * FH; e += NT) {
+            const uint32_t side = e / FH, r = e - side * FH;  // side 0: + faces, 1: - faces
+            uint32_t dir, lx, ly, lz;
+            if (r < FX) dir = 0, ly = r % TY, lz = r / TY, lx = side ? 0 : TX - 1;
+            else if (r < FX + FY) dir = 1, lx = (r - FX) % TX, lz = (r - FX) / TX, ly = side ? 0 : TY - 1;
+            else dir = 2, lx = (r - FX - FY) % TX, ly = (r - FX - FY) / TX, lz = side ? 0 : TZ - 1;
+            if (!((has_n >> (dir + 3 * side)) & 1u) || lx >= wx || ly >= wy || lz >= wz) continue;
+            const uint32_t l = lx + TX * (ly + TY * lz);
+            const uint32_t ga = gid(l);
+            const uint64_t step = dir == 0 ? 1ull : dir == 1 ? (uint64_t)nx : nxy;
+            const uint32_t gb = side ? (uint32_t)(ga - step) : (uint32_t)(ga + step);
+            const uint32_t kb = order_key(__ldg(f + gb)), ka = K[l];
+            uint32_t kS = ka, gS = ga;  // level: the later end of the edge
+            if (kbefore(ka, ga, kb, gb)) kS = kb, gS = gb;
+            uint32_t x = l;
+            for (uint32_t h = 0; h < (uint32_t)TV; h++) {
+                const uint32_t w = vT[x];
+                if (w == sm_pack(x, x)) break;
+                const uint32_t sv = sm_s(w);
+                if (kbefore(kS, gS, K[sv], gid(sv))) break;  // link above the level
+                x = sm_v(w);
+            }
+            out[e] = gid(x);
+        }
+    }
+
     // 7. write the tile's triplets with global ids (coalesced rows)
     if (vec) {
         for (uint32_t q = threadIdx.x; q < TV / 2; q += NT) {
@@ -448,16 +486,26 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 2 : 1536 / NT) k_tile(Loc loc
 //
 // The rest of the edge loop of Algorithm 1: the edges between neighbouring
 // tiles, merged with 64-bit CAS on the global triplets (Algorithms 2, 3).
-// CTA t takes the edges from tile t to its +x, +y, +z neighbour tiles, so
-// the climbs of one CTA stay mostly within a few tiles' entries (L2 reuse).
-// A merge for edge (a, b) at level S = the later of a, b starts at a and b
-// themselves; their tile triplets lead to the tile-local deepest vertices.
+// CTA t takes the edges from tile t to its +x, +y, +z neighbour tiles. k_tile
+// left, for both ends of every such edge (a, b) at level S, the tile-local
+// top of the end at S (the deepest vertex of its tile component below S). Two
+// edges whose ends have the same pair of tops join the same two tile
+// components, and the later of the two is already represented once the
+// earlier is merged, so the CTA keeps, per pair of tops, only the edge with
+// the earliest level (a shared-memory hash with 64-bit atomicMin on
+// (key, id) of S) and merges that one, starting its climbs at the tops.
+constexpr uint32_t kCrossHash = 2048;
+
 template <int LX, int LY, int LZ, class Loc>
 __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
 {
     if (*status) return;
     using TS = Tile<LX, LY, LZ>;
     constexpr uint32_t TX = TS::TX, TY = TS::TY, TZ = TS::TZ;
+    constexpr uint32_t FX = TY * TZ, FY = TX * TZ, FZ = TX * TY, FH = FX + FY + FZ;
+    static_assert(FH <= kCrossHash / 3 * 2, "hash load factor");
+    constexpr unsigned long long EMPTY = ~0ull;
+    __shared__ unsigned long long hkey[kCrossHash], hval[kCrossHash];
     uint32_t tile;
     const FieldDesc fd = loc.tile(blockIdx.x, tile);
     uint64_t *W = fd.W;
@@ -468,26 +516,60 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
     const uint32_t wx = min(TX, nx - x0), wy = min(TY, ny - y0), wz = min(TZ, nz - z0);
     const uint32_t nxy = nx * ny;
     const uint32_t base = z0 * nxy + y0 * nx + x0;
-    const uint32_t cx = (x0 + TX < nx) ? wy * wz : 0;
-    const uint32_t cy = (y0 + TY < ny) ? wx * wz : 0;
-    const uint32_t cz = (z0 + TZ < nz) ? wx * wy : 0;
-    bool ok = true;
-    for (uint32_t e = threadIdx.x; e < cx + cy + cz; e += blockDim.x) {
-        uint32_t a, b;
-        if (e < cx) {
-            a = base + (e / wy) * nxy + (e % wy) * nx + (TX - 1);
+    const uint32_t *fa = fd.faces + (size_t)tile * (2 * FH);
+    const uint32_t *fbx = fd.faces + (size_t)(tile + 1) * (2 * FH) + FH;
+    const uint32_t *fby = fd.faces + (size_t)(tile + ntx) * (2 * FH) + FH + FX;
+    const uint32_t *fbz = fd.faces + (size_t)(tile + ntx * nty) * (2 * FH) + FH + FX + FY;
+    for (uint32_t i = threadIdx.x; i < kCrossHash; i += blockDim.x) hkey[i] = EMPTY, hval[i] = EMPTY;
+    __syncthreads();
+    const bool hx = x0 + TX < nx, hy = y0 + TY < ny, hz = z0 + TZ < nz;
+    for (uint32_t e = threadIdx.x; e < FH; e += blockDim.x) {
+        uint32_t a, b, ta, tb;
+        if (e < FX) {
+            const uint32_t ly = e % TY, lz = e / TY;
+            if (!hx || ly >= wy || lz >= wz) continue;
+            a = base + lz * nxy + ly * nx + (TX - 1);
             b = a + 1;
-        } else if (e < cx + cy) {
-            const uint32_t k = e - cx;
-            a = base + (k / wx) * nxy + (TY - 1) * nx + (k % wx);
+            ta = fa[e];
+            tb = fbx[e];
+        } else if (e < FX + FY) {
+            const uint32_t k = e - FX, lx = k % TX, lz = k / TX;
+            if (!hy || lx >= wx || lz >= wz) continue;
+            a = base + lz * nxy + (TY - 1) * nx + lx;
             b = a + nx;
+            ta = fa[e];
+            tb = fby[k];
         } else {
-            const uint32_t k = e - cx - cy;
-            a = base + (TZ - 1) * nxy + (k / wx) * nx + (k % wx);
+            const uint32_t k = e - FX - FY, lx = k % TX, ly = k / TX;
+            if (!hz || lx >= wx || ly >= wy) continue;
+            a = base + (TZ - 1) * nxy + ly * nx + lx;
             b = a + nxy;
+            ta = fa[e];
+            tb = fbz[k];
         }
-        const uint32_t S = before(__ldg(f + b), b, __ldg(f + a), a) ? a : b;
-        ok &= merge(W, f, S, a, b);
+        const float va = __ldg(f + a), vb = __ldg(f + b);
+        const uint32_t S = before(vb, b, va, a) ? a : b;
+        const float vS = S == a ? va : vb;
+        const unsigned long long key = ((unsigned long long)ta << 32) | tb;
+        const uint32_t bits = vS == 0.0f ? 0u : __float_as_uint(vS);
+        const uint32_t kS = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+        const unsigned long long val = ((unsigned long long)kS << 32) | S;
+        uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 53) & (kCrossHash - 1);
+        for (uint32_t p = 0; p < kCrossHash; p++) {
+            const unsigned long long k0 = atomicCAS(&hkey[h], EMPTY, key);
+            if (k0 == EMPTY || k0 == key) {
+                atomicMin(&hval[h], val);
+                break;
+            }
+            h = (h + 1) & (kCrossHash - 1);
+        }
+    }
+    __syncthreads();
+    bool ok = true;
+    for (uint32_t i = threadIdx.x; i < kCrossHash; i += blockDim.x) {
+        const unsigned long long key = hkey[i];
+        if (key == EMPTY) continue;
+        ok &= merge(W, f, (uint32_t)hval[i], (uint32_t)(key >> 32), (uint32_t)key);
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
 }
@@ -564,6 +646,20 @@ void tile_shape(int variant, uint32_t &tx, uint32_t &ty, uint32_t &tz)
     }
 }
 
+uint32_t face_words(int variant)
+{
+    uint32_t tx, ty, tz;
+    tile_shape(variant, tx, ty, tz);
+    return 2 * (ty * tz + tx * tz + tx * ty);
+}
+
+uint64_t tile_count(int variant, uint32_t nx, uint32_t ny, uint32_t nz)
+{
+    uint32_t tx, ty, tz;
+    tile_shape(variant, tx, ty, tz);
+    return (uint64_t)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * ((nz + tz - 1) / tz);
+}
+
 template <int V, class Loc>
 static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, int persistent_grid, uint32_t *status,
                              cudaStream_t st)
@@ -602,13 +698,14 @@ static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, i
 }
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         cudaStream_t st)
+                         uint32_t *faces, cudaStream_t st)
 {
     using VV = Variant<0>;
     OneField loc;
     loc.d = FieldDesc{};
     loc.d.f = f;
     loc.d.W = W;
+    loc.d.faces = faces;
     loc.d.nx = nx, loc.d.ny = ny, loc.d.nz = nz;
     loc.d.n = (uint64_t)nx * ny * nz;
     loc.d.ntx = (nx + (1u << VV::LX) - 1) >> VV::LX;

@@ -18,6 +18,7 @@ struct FieldDesc {
     uint64_t *W;       // triplets, field-local vertex ids
     uint32_t *pairs;   // pair output ([cap][2]) or null
     uint64_t *meta;    // [0] npairs, [1] number of roots, [2] root
+    uint32_t *faces;   // per tile: tile-local tops of the cross-edge ends, or null
     uint64_t n, cap;   // vertices, pair capacity
     uint64_t chunk0;   // first compaction chunk of the field
     uint32_t nx, ny, nz;
@@ -29,7 +30,8 @@ struct FieldDesc {
 struct Workspace {
     uint32_t *status;  // status bits (ST_*)
     uint32_t *more;    // "another round needed" flag of iterative kernels
-    uint64_t *meta;    // [0] npairs, [1] number of roots, [2] root vertex
+    uint64_t *meta;    // [0] npairs, [1] number of roots, [2] root
+    uint32_t *faces;   // per tile: tile-local tops of the cross-edge ends, or null vertex
     uint32_t *counts;  // per-chunk counts, then exclusive offsets in place
     uint64_t nchunks;
 };
@@ -51,12 +53,20 @@ class PhaseScope {
     void *a_;
 };
 
+// The pair-compaction part of a workspace (status, counters, chunk counts)...
 size_t workspace_bytes(uint64_t n);
 bool carve_workspace(void *base, size_t bytes, uint64_t n, Workspace &ws);
+// ...and the whole workspace a build needs: that part followed by the face
+// buffers of k_tile / k_cross (build_faces points at them).
+size_t build_workspace_bytes(uint32_t nx, uint32_t ny, uint32_t nz);
+uint32_t *build_faces(void *base, uint64_t n);
+// u32 entries of one tile's face buffer for tile variant v, and tile counts
+uint32_t face_words(int variant);
+uint64_t tile_count(int variant, uint32_t nx, uint32_t ny, uint32_t nz);
 int device_sms();
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         cudaStream_t st);
+                         uint32_t *faces, cudaStream_t st);
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
                          cudaStream_t st);
 
