@@ -138,7 +138,7 @@ __device__ __forceinline__ void sm_merge(uint32_t *T, const uint32_t *K, uint32_
     ok = false;
 }
 
-template <int LX, int LY, int LZ, int NT, int NB>
+template <int LX, int LY, int LZ, int NT, int NB, bool FULL>
 __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, uint32_t *status)
 {
     const float *__restrict__ f = fd.f;
@@ -165,17 +165,17 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
-    const uint32_t wx = min((uint32_t)TX, nx - x0), wy = min((uint32_t)TY, ny - y0),
-                   wz = min((uint32_t)TZ, nz - z0);
-    const uint64_t nxy = (uint64_t)nx * ny;
-    const uint64_t base = (uint64_t)z0 * nxy + (uint64_t)y0 * nx + x0;
+    // a FULL tile lies inside the grid: its extents are the tile's
+    const uint32_t wx = FULL ? (uint32_t)TX : min((uint32_t)TX, nx - x0),
+                   wy = FULL ? (uint32_t)TY : min((uint32_t)TY, ny - y0),
+                   wz = FULL ? (uint32_t)TZ : min((uint32_t)TZ, nz - z0);
+    const uint32_t nxy = nx * ny;  // n < 2^32, so every id fits 32 bits
+    const uint32_t base = z0 * nxy + y0 * nx + x0;
     auto lxo = [](uint32_t l) { return l & (TX - 1); };
     auto lyo = [](uint32_t l) { return (l >> LX) & (TY - 1); };
     auto lzo = [](uint32_t l) { return l >> (LX + LY); };
-    auto valid = [&](uint32_t l) { return lxo(l) < wx && lyo(l) < wy && lzo(l) < wz; };
-    auto gid = [&](uint32_t l) {
-        return (uint32_t)(base + (uint64_t)lzo(l) * nxy + (uint64_t)lyo(l) * nx + lxo(l));
-    };
+    auto valid = [&](uint32_t l) { return FULL || (lxo(l) < wx && lyo(l) < wy && lzo(l) < wz); };
+    auto gid = [&](uint32_t l) { return base + lzo(l) * nxy + lyo(l) * nx + lxo(l); };
     if (threadIdx.x == 0) {
         s_kmin = 0xFFFFFFFFu, s_kmax = 0, s_qlen = 0;
         s_nvalid = wx * wy * wz;
@@ -190,7 +190,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     if (vec) {
         for (uint32_t q = threadIdx.x; q < TV / 4; q += NT) {
             const uint32_t l = 4 * q;
-            if (lxo(l) < wx && lyo(l) < wy && lzo(l) < wz) {
+            if (valid(l)) {
                 const float4 v = __ldg(reinterpret_cast<const float4 *>(f + gid(l)));
                 bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
                 const uint4 k = make_uint4(order_key(v.x), order_key(v.y), order_key(v.z), order_key(v.w));
@@ -421,8 +421,8 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
             if (!((has_n >> (dir + 3 * side)) & 1u) || lx >= wx || ly >= wy || lz >= wz) continue;
             const uint32_t l = lx + TX * (ly + TY * lz);
             const uint32_t ga = gid(l);
-            const uint64_t step = dir == 0 ? 1ull : dir == 1 ? (uint64_t)nx : nxy;
-            const uint32_t gb = side ? (uint32_t)(ga - step) : (uint32_t)(ga + step);
+            const uint32_t step = dir == 0 ? 1u : dir == 1 ? nx : nxy;
+            const uint32_t gb = side ? ga - step : ga + step;
             const uint32_t kb = order_key(__ldg(f + gb)), ka = K[l];
             uint32_t kS = ka, gS = ga;  // level: the later end of the edge
             if (kbefore(ka, ga, kb, gb)) kS = kb, gS = gb;
@@ -457,15 +457,17 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
 }
 
 // One CTA per tile (queue == null), or a persistent grid that takes tiles
-// from a device-side counter until none is left (the batched build).
-template <int LX, int LY, int LZ, int NT, int NB, class Loc>
+// from a device-side counter until none is left (the batched build). FULL is
+// set when every tile lies inside the grid (grid sides multiples of the tile
+// sides), which drops all partial-tile bounds checks.
+template <int LX, int LY, int LZ, int NT, int NB, class Loc, bool FULL>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 2 : 1536 / NT) k_tile(Loc loc, uint32_t ntiles, uint32_t *queue,
                                                                       uint32_t *status)
 {
     if (queue == nullptr) {
         uint32_t local;
         const FieldDesc fd = loc.tile(blockIdx.x, local);
-        tile_body<LX, LY, LZ, NT, NB>(fd, local, status);
+        tile_body<LX, LY, LZ, NT, NB, FULL>(fd, local, status);
         return;
     }
     __shared__ uint32_t s_next;
@@ -477,7 +479,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 2 : 1536 / NT) k_tile(Loc loc
         if (t >= ntiles) break;
         uint32_t local;
         const FieldDesc fd = loc.tile(t, local);
-        tile_body<LX, LY, LZ, NT, NB>(fd, local, status);
+        tile_body<LX, LY, LZ, NT, NB, FULL>(fd, local, status);
         __syncthreads();
     }
 }
@@ -660,28 +662,40 @@ uint64_t tile_count(int variant, uint32_t nx, uint32_t ny, uint32_t nz)
     return (uint64_t)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * ((nz + tz - 1) / tz);
 }
 
-template <int V, class Loc>
-static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, int persistent_grid, uint32_t *status,
-                             cudaStream_t st)
+template <int V, class Loc, bool FULL>
+static cudaError_t tile_attrs()
 {
     using VV = Variant<V>;
     using TS = Tile<VV::LX, VV::LY, VV::LZ, VV::NT>;
-    auto ktile = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, Loc>;
+    static bool done = false;  // per instantiation
+    if (done) return cudaSuccess;
+    auto ktile = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, Loc, FULL>;
+    cudaError_t e = cudaFuncSetAttribute(ktile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS::kSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(ktile, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    done = true;
+    return cudaSuccess;
+}
+
+template <int V, class Loc>
+static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, int persistent_grid, bool full,
+                             uint32_t *status, cudaStream_t st)
+{
+    using VV = Variant<V>;
+    using TS = Tile<VV::LX, VV::LY, VV::LZ, VV::NT>;
     const size_t smem = TS::kSmem;
-    static bool attr_done = false;  // per instantiation
     cudaError_t e;
-    if (!attr_done) {
-        if ((e = cudaFuncSetAttribute(ktile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-            return e;
-        if ((e = cudaFuncSetAttribute(ktile, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
-            return e;
-        attr_done = true;
-    }
+    if ((e = full ? tile_attrs<V, Loc, true>() : tile_attrs<V, Loc, false>()) != cudaSuccess) return e;
     {
         PhaseScope ps(kTile, st);
         const unsigned grid = queue ? (unsigned)persistent_grid : ntiles;
-        ktile<<<grid, VV::NT, smem, st>>>(loc, ntiles, queue, status);
+        if (full)
+            k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, Loc, true><<<grid, VV::NT, smem, st>>>(loc, ntiles, queue,
+                                                                                                 status);
+        else
+            k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, Loc, false><<<grid, VV::NT, smem, st>>>(loc, ntiles,
+                                                                                                  queue, status);
         count_launch();
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -712,7 +726,8 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
     loc.d.nty = (ny + (1u << VV::LY) - 1) >> VV::LY;
     const uint32_t ntz = (nz + (1u << VV::LZ) - 1) >> VV::LZ;
     const uint64_t ntiles = (uint64_t)loc.d.ntx * loc.d.nty * ntz;
-    return run_build<0>(loc, (uint32_t)ntiles, nullptr, 0, ws.status, st);
+    const bool full = nx % (1u << VV::LX) == 0 && ny % (1u << VV::LY) == 0 && nz % (1u << VV::LZ) == 0;
+    return run_build<0>(loc, (uint32_t)ntiles, nullptr, 0, full, ws.status, st);
 }
 
 cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint32_t ntiles, int variant,
@@ -724,8 +739,8 @@ cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint3
     // persistent grid: as many CTAs as fit on the GPU at once
     const int per_sm = variant == 1 ? 1536 / Variant<1>::NT : 2;
     const int grid = device_sms() * per_sm;
-    if (variant == 1) return run_build<1>(loc, ntiles, queue, grid, status, st);
-    return run_build<0>(loc, ntiles, queue, grid, status, st);
+    if (variant == 1) return run_build<1>(loc, ntiles, queue, grid, false, status, st);
+    return run_build<0>(loc, ntiles, queue, grid, false, status, st);
 }
 
 }  // namespace mt
