@@ -88,6 +88,16 @@ size_t mt_workspace_bytes(mt_grid g);
  */
 mt_status mt_build_triplets(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, void *stream);
 
+/* Flags of the _ex calls. MT_SUPERLEVEL: work on the superlevel sets of f,
+ * i.e. build the merge tree of -f (the "split tree" of Section 4's setup,
+ * the tree the paper's experiments report): minima of -f are maxima of f, and
+ * the order is (-f[a], a). mt_components_at_ex with the flag labels the
+ * components of {u : f[u] >= t}. The result equals the plain call on -f. */
+#define MT_SUPERLEVEL 1u
+
+mt_status mt_build_triplets_ex(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
+                               void *stream);
+
 /*
  * 0-dimensional persistence pairs of the tree in d_W (Section 1: one point
  * (f(a), f(b)) per branch, a a minimum and b the saddle where it merges).
@@ -112,6 +122,9 @@ mt_status mt_persistence_pairs(const float *d_f, const uint64_t *d_W, mt_grid g,
  */
 mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t *d_labels,
                            void *d_ws, size_t ws_bytes, void *stream);
+
+mt_status mt_components_at_ex(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t flags,
+                              uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
  * Synchronise `stream` and return (then clear) the workspace status word:

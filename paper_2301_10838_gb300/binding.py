@@ -33,6 +33,9 @@ __all__ = [
     "mt_persistence_pairs",
     "mt_components_at",
     "mt_sync_status",
+    "MT_SUPERLEVEL",
+    "mt_build_triplets_ex",
+    "mt_components_at_ex",
     "mt_persistence_pairs_noalloc",
     "BatchPlan",
     "mt_batch_workspace_bytes",
@@ -53,6 +56,7 @@ __all__ = [
 ]
 
 MT_OK = 0
+MT_SUPERLEVEL = 1  # flag of the _ex calls: the tree of -f (superlevel sets, the split tree)
 STATUS_NAMES = {0: "MT_OK", -1: "MT_ERR_INVALID", -2: "MT_ERR_TOO_LARGE", -3: "MT_ERR_NONFINITE",
                 -4: "MT_ERR_CAPACITY", -5: "MT_ERR_CUDA", -6: "MT_ERR_NOMEM", -7: "MT_ERR_TIMEOUT",
                 -8: "MT_ERR_BUSY"}
@@ -91,6 +95,9 @@ _SIGS = {
     "mt_persistence_pairs": ([_P, _P, Grid, _P, _U64, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_components_at": ([_P, _P, Grid, ctypes.c_float, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_sync_status": ([_P, _P], ctypes.c_int32),
+    "mt_build_triplets_ex": ([_P, Grid, _P, _P, ctypes.c_size_t, ctypes.c_uint32, _P], ctypes.c_int32),
+    "mt_components_at_ex": ([_P, _P, Grid, ctypes.c_float, ctypes.c_uint32, _P, _P, ctypes.c_size_t, _P],
+                            ctypes.c_int32),
     "mt_persistence_pairs_noalloc": ([_P, _P, Grid, _P, _U64, _P, _P, _P], ctypes.c_int32),
     "mt_batch_workspace_bytes": ([_P, ctypes.c_uint32], ctypes.c_size_t),
     "mt_batch_prepare": ([_P, _P, ctypes.c_uint32, _P, _P, _P, ctypes.c_size_t, _P, _P], ctypes.c_int32),
@@ -190,6 +197,26 @@ def mt_build_triplets(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, stream
     pW = _dev(W, "W", _I64, n)
     pws = _dev(ws, "ws", (torch.uint8,))
     _check(load().mt_build_triplets(pf, g, pW, pws, ws.numel(), _stream_ptr(stream)), "mt_build_triplets")
+
+
+def mt_build_triplets_ex(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, flags: int, stream=None) -> None:
+    """mt_build_triplets with flags (MT_SUPERLEVEL: the split tree, i.e. the
+    merge tree of -f)."""
+    g = grid_of(f)
+    n = f.numel()
+    _check(load().mt_build_triplets_ex(_dev(f, "f", (torch.float32,)), g, _dev(W, "W", _I64, n),
+                                       _dev(ws, "ws", (torch.uint8,)), ws.numel(), int(flags), _stream_ptr(stream)),
+           "mt_build_triplets_ex")
+
+
+def mt_components_at_ex(f: torch.Tensor, W: torch.Tensor, t: float, flags: int, labels: torch.Tensor,
+                        ws: torch.Tensor, stream=None) -> None:
+    """mt_components_at with flags (MT_SUPERLEVEL: components of f >= t)."""
+    g = grid_of(f)
+    n = f.numel()
+    _check(load().mt_components_at_ex(_dev(f, "f", (torch.float32,)), _dev(W, "W", _I64, n), g, float(t),
+                                      int(flags), _dev(labels, "labels", _I32, n), _dev(ws, "ws", (torch.uint8,)),
+                                      ws.numel(), _stream_ptr(stream)), "mt_components_at_ex")
 
 
 def mt_persistence_pairs(f: torch.Tensor, W: torch.Tensor, pairs: torch.Tensor, ws: torch.Tensor,

@@ -101,19 +101,28 @@ size_t mt_workspace_bytes(mt_grid g)
     return build_workspace_bytes(g.nx, g.ny, g.nz);
 }
 
-mt_status mt_build_triplets(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, void *stream)
+mt_status mt_build_triplets_ex(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
+                               void *stream)
 {
     uint64_t n;
     mt_status st = grid_n(g, n);
     if (st != MT_OK) return st;
-    if (!d_f || !d_W || ((uintptr_t)d_f & 3) || ((uintptr_t)d_W & 7)) return MT_ERR_INVALID;
+    if (!d_f || !d_W || ((uintptr_t)d_f & 3) || ((uintptr_t)d_W & 7) || (flags & ~MT_SUPERLEVEL))
+        return MT_ERR_INVALID;
     Workspace ws;
     if (ws_bytes < build_workspace_bytes(g.nx, g.ny, g.nz) || !carve_workspace(d_ws, ws_bytes, n, ws))
         return MT_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(ws.status, 0, 256, s) != cudaSuccess) return MT_ERR_CUDA;
-    if (launch_build(d_f, d_W, g.nx, g.ny, g.nz, ws, build_faces(d_ws, n), s) != cudaSuccess) return MT_ERR_CUDA;
+    const float sg = (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f;
+    if (launch_build(d_f, d_W, g.nx, g.ny, g.nz, ws, build_faces(d_ws, n), sg, s) != cudaSuccess)
+        return MT_ERR_CUDA;
     return MT_OK;
+}
+
+mt_status mt_build_triplets(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, void *stream)
+{
+    return mt_build_triplets_ex(d_f, g, d_W, d_ws, ws_bytes, 0u, stream);
 }
 
 mt_status mt_persistence_pairs(const float *d_f, const uint64_t *d_W, mt_grid g, uint32_t *d_pairs, uint64_t cap,
@@ -141,19 +150,28 @@ mt_status mt_persistence_pairs(const float *d_f, const uint64_t *d_W, mt_grid g,
     return meta[0] > cap ? MT_ERR_CAPACITY : MT_OK;
 }
 
-mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t *d_labels,
-                           void *d_ws, size_t ws_bytes, void *stream)
+mt_status mt_components_at_ex(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t flags,
+                              uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream)
 {
     uint64_t n;
     mt_status st = grid_n(g, n);
     if (st != MT_OK) return st;
-    if (!d_f || !d_W || !d_labels || std::isnan(t) || ((uintptr_t)d_W & 7) || ((uintptr_t)d_labels & 3))
+    if (!d_f || !d_W || !d_labels || std::isnan(t) || ((uintptr_t)d_W & 7) || ((uintptr_t)d_labels & 3) ||
+        (flags & ~MT_SUPERLEVEL))
         return MT_ERR_INVALID;
     Workspace ws;
     if (!carve_workspace(d_ws, ws_bytes, n, ws)) return MT_ERR_INVALID;
-    if (launch_labels(d_f, d_W, g.nx, g.ny, g.nz, t, d_labels, ws, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    const float sg = (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f;
+    if (launch_labels(d_f, d_W, g.nx, g.ny, g.nz, sg * t, sg, d_labels, ws, static_cast<cudaStream_t>(stream)) !=
+        cudaSuccess)
         return MT_ERR_CUDA;
     return MT_OK;
+}
+
+mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t *d_labels,
+                           void *d_ws, size_t ws_bytes, void *stream)
+{
+    return mt_components_at_ex(d_f, d_W, g, t, 0u, d_labels, d_ws, ws_bytes, stream);
 }
 
 mt_status mt_sync_status(void *d_ws, void *stream)

@@ -101,7 +101,7 @@ mt_status mt_batch_prepare(const float *d_arena, const mt_grid *h_grids, uint32_
         uint32_t tile0 = 0;
         for (uint32_t i = 0; i < nfields; i++) {
             FieldDesc &d = host[(size_t)v * nfields + i];
-            std::memset(&d, 0, sizeof(d));
+            d = FieldDesc{};
             const mt_grid &g = h_grids[i];
             d.n = (uint64_t)g.nx * g.ny * g.nz;
             d.f = d_arena + off;

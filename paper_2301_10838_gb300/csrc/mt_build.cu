@@ -142,6 +142,7 @@ template <int LX, int LY, int LZ, int NT, int NB, bool FULL>
 __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, uint32_t *status)
 {
     const float *__restrict__ f = fd.f;
+    const float sg = fd.sg;
     uint64_t *__restrict__ W = fd.W;
     const uint32_t nx = fd.nx, ny = fd.ny, nz = fd.nz, ntx = fd.ntx, nty = fd.nty;
     const bool vec = (nx % 4 == 0) && ((uintptr_t)f % 16 == 0) && ((uintptr_t)W % 16 == 0);
@@ -191,7 +192,8 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
         for (uint32_t q = threadIdx.x; q < TV / 4; q += NT) {
             const uint32_t l = 4 * q;
             if (valid(l)) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(f + gid(l)));
+                float4 v = __ldg(reinterpret_cast<const float4 *>(f + gid(l)));
+                v.x *= sg, v.y *= sg, v.z *= sg, v.w *= sg;
                 bad |= !isfinite(v.x) | !isfinite(v.y) | !isfinite(v.z) | !isfinite(v.w);
                 const uint4 k = make_uint4(order_key(v.x), order_key(v.y), order_key(v.z), order_key(v.w));
                 kmin = min(kmin, min(min(k.x, k.y), min(k.z, k.w)));
@@ -202,7 +204,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     } else {
         for (uint32_t l = threadIdx.x; l < TV; l += NT) {
             if (valid(l)) {
-                const float v = __ldg(f + gid(l));
+                const float v = sg * __ldg(f + gid(l));
                 bad |= !isfinite(v);
                 const uint32_t k = order_key(v);
                 kmin = min(kmin, k);
@@ -423,7 +425,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
             const uint32_t ga = gid(l);
             const uint32_t step = dir == 0 ? 1u : dir == 1 ? nx : nxy;
             const uint32_t gb = side ? ga - step : ga + step;
-            const uint32_t kb = order_key(__ldg(f + gb)), ka = K[l];
+            const uint32_t kb = order_key(sg * __ldg(f + gb)), ka = K[l];
             uint32_t kS = ka, gS = ga;  // level: the later end of the edge
             if (kbefore(ka, ga, kb, gb)) kS = kb, gS = gb;
             uint32_t x = l;
@@ -511,7 +513,7 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
     uint32_t tile;
     const FieldDesc fd = loc.tile(blockIdx.x, tile);
     uint64_t *W = fd.W;
-    const float *__restrict__ f = fd.f;
+    const Field f{fd.f, fd.sg};
     const uint32_t nx = fd.nx, ny = fd.ny, nz = fd.nz, ntx = fd.ntx, nty = fd.nty;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
             ta = fa[e];
             tb = fbz[k];
         }
-        const float va = __ldg(f + a), vb = __ldg(f + b);
+        const float va = f[a], vb = f[b];
         const uint32_t S = before(vb, b, va, a) ? a : b;
         const float vS = S == a ? va : vb;
         const unsigned long long key = ((unsigned long long)ta << 32) | tb;
@@ -597,7 +599,7 @@ __global__ void __launch_bounds__(NT) k_repair(Loc loc, uint32_t *status)
     uint32_t tile;
     const FieldDesc fd = loc.tile(blockIdx.x, tile);
     uint64_t *W = fd.W;
-    const float *__restrict__ f = fd.f;
+    const Field f{fd.f, fd.sg};
     const uint32_t nx = fd.nx, ny = fd.ny, nz = fd.nz, ntx = fd.ntx, nty = fd.nty;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(NT) k_repair(Loc loc, uint32_t *status)
             const uint32_t s = tri_s(T), t = tri_v(T);
             if (pass == 0 ? (s == u) : (s != u || t == u)) continue;
             uint32_t steps = 0;
-            const uint32_t r = representative_cached(W, f, t, s, __ldg(f + s), steps);
+            const uint32_t r = representative_cached(W, f, t, s, f[s], steps);
             if (steps > kChaseLimit) {
                 ok = false;
                 continue;
@@ -712,7 +714,7 @@ static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, i
 }
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         uint32_t *faces, cudaStream_t st)
+                         uint32_t *faces, float sg, cudaStream_t st)
 {
     using VV = Variant<0>;
     OneField loc;
@@ -720,6 +722,7 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
     loc.d.f = f;
     loc.d.W = W;
     loc.d.faces = faces;
+    loc.d.sg = sg;
     loc.d.nx = nx, loc.d.ny = ny, loc.d.nz = nz;
     loc.d.n = (uint64_t)nx * ny * nz;
     loc.d.ntx = (nx + (1u << VV::LX) - 1) >> VV::LX;

@@ -52,19 +52,28 @@ __device__ __forceinline__ uint64_t cas_tri(uint64_t *p, uint64_t expect, uint64
 
 __device__ __forceinline__ void raise_status(uint32_t *status, uint32_t bit) { atomicOr(status, bit); }
 
+// The values as the order sees them: f itself (sublevel sets), or -f (sg =
+// -1) for the tree of the superlevel sets, the split tree. Multiplying by -1
+// is exact, and -0 still equals +0.
+struct Field {
+    const float *f;
+    float sg;
+    __device__ __forceinline__ float operator[](uint32_t i) const { return sg * __ldg(f + i); }
+};
+
 // Follow the triplet links from x while the link's saddle is at or below
 // level S (vertex order), i.e. walk to the deepest vertex that the current
 // tree connects to x below S (the climbs of Algorithm 3). Returns the word
 // of the vertex where it stops and leaves that vertex in x. A root word
 // (x, x) always stops the walk (the paper's pseudocode has no guard for it).
-__device__ __forceinline__ uint64_t climb(const uint64_t *W, const float *f, uint32_t &x, uint32_t S, float fS,
+__device__ __forceinline__ uint64_t climb(const uint64_t *W, const Field f, uint32_t &x, uint32_t S, float fS,
                                           uint32_t &steps)
 {
     uint64_t T = ld_tri(W + x);
     for (;;) {
         const uint32_t s = tri_s(T), t = tri_v(T);
         if (s == x && t == x) break;  // root
-        if (s != S && !before(__ldg(f + s), s, fS, S)) break;  // saddle above S
+        if (s != S && !before(f[s], s, fS, S)) break;  // saddle above S
         x = t;
         T = ld_tri(W + x);
         if (++steps > kMergeStepLimit) break;
@@ -83,9 +92,9 @@ __device__ __forceinline__ uint64_t climb(const uint64_t *W, const float *f, uin
 //      carries no link, so the merge ends there.)
 //   5. if the CAS fails another thread moved v first: climb again.
 // Returns false if the step budget ran out.
-__device__ __forceinline__ bool merge(uint64_t *W, const float *f, uint32_t S, uint32_t a, uint32_t b)
+__device__ __forceinline__ bool merge(uint64_t *W, const Field f, uint32_t S, uint32_t a, uint32_t b)
 {
-    float fS = __ldg(f + S);
+    float fS = f[S];
     uint32_t u = a, v = b;
     uint32_t steps = 0;
     for (;;) {
@@ -93,7 +102,7 @@ __device__ __forceinline__ bool merge(uint64_t *W, const float *f, uint32_t S, u
         uint64_t Tv = climb(W, f, v, S, fS, steps);
         if (++steps > kMergeStepLimit) return false;
         if (u == v) return true;
-        if (before(__ldg(f + v), v, __ldg(f + u), u)) {
+        if (before(f[v], v, f[u], u)) {
             uint32_t tx = u;
             u = v;
             v = tx;
@@ -106,7 +115,7 @@ __device__ __forceinline__ bool merge(uint64_t *W, const float *f, uint32_t S, u
             const uint32_t sv = tri_s(Tv), tv = tri_v(Tv);
             if (sv == v && tv == v) return true;  // displaced a root
             S = sv;
-            fS = __ldg(f + sv);
+            fS = f[sv];
             v = tv;
         }
     }
@@ -117,14 +126,14 @@ __device__ __forceinline__ bool merge(uint64_t *W, const float *f, uint32_t S, u
 // s' <= S in the vertex order and returns the vertex where it stops (the
 // printed algorithm returns one hop further; the vertex itself is the one
 // the definition asks for).
-__device__ __forceinline__ uint32_t representative(const uint64_t *W, const float *f, uint32_t x, uint32_t S, float fS,
+__device__ __forceinline__ uint32_t representative(const uint64_t *W, const Field f, uint32_t x, uint32_t S, float fS,
                                                    uint32_t &steps)
 {
     for (;;) {
         const uint64_t T = ld_tri(W + x);
         const uint32_t s = tri_s(T), t = tri_v(T);
         if (s == x && t == x) return x;
-        if (s != S && !before(__ldg(f + s), s, fS, S)) return x;
+        if (s != S && !before(f[s], s, fS, S)) return x;
         x = t;
         if (++steps > kChaseLimit) return x;
     }
@@ -133,14 +142,14 @@ __device__ __forceinline__ uint32_t representative(const uint64_t *W, const floa
 // The same chase with ordinary (L1-cacheable) loads, for passes in which the
 // entries only ever move further along their own chains (repair): a stale
 // copy then still leads to the same representative.
-__device__ __forceinline__ uint32_t representative_cached(const uint64_t *W, const float *f, uint32_t x, uint32_t S,
+__device__ __forceinline__ uint32_t representative_cached(const uint64_t *W, const Field f, uint32_t x, uint32_t S,
                                                           float fS, uint32_t &steps)
 {
     for (;;) {
         const uint64_t T = W[x];
         const uint32_t s = tri_s(T), t = tri_v(T);
         if (s == x && t == x) return x;
-        if (s != S && !before(__ldg(f + s), s, fS, S)) return x;
+        if (s != S && !before(f[s], s, fS, S)) return x;
         x = t;
         if (++steps > kChaseLimit) return x;
     }

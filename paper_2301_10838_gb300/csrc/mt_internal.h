@@ -24,6 +24,7 @@ struct FieldDesc {
     uint32_t nx, ny, nz;
     uint32_t ntx, nty; // tiles along x and y for the tile shape in use
     uint32_t tile0;    // first tile of the field
+    float sg = 1.0f;   // -1: the tree of -f (superlevel sets)
 };
 
 // Views into the caller's workspace (layout fixed by carve_workspace).
@@ -66,7 +67,7 @@ uint64_t tile_count(int variant, uint32_t nx, uint32_t ny, uint32_t nz);
 int device_sms();
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         uint32_t *faces, cudaStream_t st);
+                         uint32_t *faces, float sg, cudaStream_t st);
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
                          cudaStream_t st);
 
@@ -78,6 +79,6 @@ cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint6
                                uint64_t *npairs, const uint32_t *status, cudaStream_t st);
 void tile_shape(int variant, uint32_t &tx, uint32_t &ty, uint32_t &tz);
 cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, float t,
-                          uint32_t *labels, Workspace &ws, cudaStream_t st);
+                          float sg, uint32_t *labels, Workspace &ws, cudaStream_t st);
 
 }  // namespace mt

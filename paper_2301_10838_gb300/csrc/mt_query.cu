@@ -187,9 +187,9 @@ cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint6
 // vertices sharing a representative find its chain in L1.
 constexpr uint32_t kLabLX = 5, kLabLY = 4, kLabLZ = 4;
 
-__global__ void __launch_bounds__(512) k_labels(const float *__restrict__ f, const uint64_t *__restrict__ W,
-                                                uint32_t nx, uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty,
-                                                float t, uint32_t *__restrict__ labels, uint32_t *status)
+__global__ void __launch_bounds__(512) k_labels(const Field f, const uint64_t *__restrict__ W, uint32_t nx,
+                                                uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty, float t,
+                                                uint32_t *__restrict__ labels, uint32_t *status)
 {
     if (*status) return;
     constexpr uint32_t TX = 1u << kLabLX, TY = 1u << kLabLY, TZ = 1u << kLabLZ, TV = TX * TY * TZ;
@@ -205,12 +205,12 @@ __global__ void __launch_bounds__(512) k_labels(const float *__restrict__ f, con
         if (lx >= wx || ly >= wy || lz >= wz) continue;
         const uint32_t u = base + lz * nxy + ly * nx + lx;
         uint32_t lab = 0xFFFFFFFFu;
-        if (__ldg(f + u) <= t) {
+        if (f[u] <= t) {
             uint32_t x = u;
             for (uint32_t h = 0;; h++) {
                 const uint64_t T = __ldg(reinterpret_cast<const unsigned long long *>(W) + x);
                 const uint32_t s = tri_s(T);
-                if (T == tri_pack(x, x) || !(__ldg(f + s) <= t)) break;
+                if (T == tri_pack(x, x) || !(f[s] <= t)) break;
                 x = tri_v(T);
                 if (h > kChaseLimit) {
                     ok = false;
@@ -225,12 +225,12 @@ __global__ void __launch_bounds__(512) k_labels(const float *__restrict__ f, con
 }
 
 cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, float t,
-                          uint32_t *labels, Workspace &ws, cudaStream_t st)
+                          float sg, uint32_t *labels, Workspace &ws, cudaStream_t st)
 {
     PhaseScope ps(kLabels, st);
     count_launch();
     const uint32_t ntx = (nx + 31) >> kLabLX, nty = (ny + 15) >> kLabLY, ntz = (nz + 15) >> kLabLZ;
-    k_labels<<<ntx * nty * ntz, 512, 0, st>>>(f, W, nx, ny, nz, ntx, nty, t, labels, ws.status);
+    k_labels<<<ntx * nty * ntz, 512, 0, st>>>(Field{f, sg}, W, nx, ny, nz, ntx, nty, t, labels, ws.status);
     return cudaGetLastError();
 }
 
