@@ -255,7 +255,10 @@ def run_ours(args):
     traffic = traffic_record(dom) if side == 1024 else None
     step_bytes = sum(ab[k] for k in ("tile", "merge", "repair", "pairs", "labels"))
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers: every step
+    # copies its field in and its triplets, pairs and labels out. Two sets of
+    # device buffers and separate copy streams let step k's copies overlap
+    # step k+1's kernels.
     e2e = None
     if not args.no_e2e:
         h_f = torch.empty(shape, dtype=torch.float32, pin_memory=True)
@@ -263,28 +266,57 @@ def run_ours(args):
         h_W = torch.empty(n, dtype=torch.int64, pin_memory=True)
         h_lab = torch.empty(n, dtype=torch.int32, pin_memory=True)
         h_pairs = torch.empty((npairs, 2), dtype=torch.int32, pin_memory=True)
-        d_f2 = torch.empty_like(f)
-        k_e2e = max(2, args.steps // 2)
+        bufs = [(f, W, labels, pairs, ws)]
+        bufs.append((torch.empty_like(f), torch.empty_like(W), torch.empty_like(labels), torch.empty_like(pairs),
+                     torch.empty_like(ws)))
+        s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        done = [torch.cuda.Event(), torch.cuda.Event()]  # buffers of slot i free again
+        for ev in done:
+            ev.record(s_out)
+        k_e2e = max(3, args.steps)
 
-        def e2e_step():
-            d_f2.copy_(h_f, non_blocking=True)
-            mt.mt_build_triplets(d_f2, W, ws)
-            np_, _ = mt.mt_persistence_pairs(d_f2, W, pairs, ws)
-            mt.mt_components_at(d_f2, W, t_thr, labels, ws)
-            h_W.copy_(W, non_blocking=True)
-            h_pairs.copy_(pairs, non_blocking=True)
-            h_lab.copy_(labels, non_blocking=True)
+        loaded = [None, None]
 
-        e2e_step()
+        def prefetch(k):
+            df = bufs[k % 2][0]
+            s_in.wait_event(done[k % 2])
+            with torch.cuda.stream(s_in):
+                df.copy_(h_f, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s_in)
+            loaded[k % 2] = ev
+
+        def e2e_step(k, last):
+            df, dW, dl, dp, dws = bufs[k % 2]
+            s_cmp.wait_event(loaded[k % 2])
+            mt.mt_build_triplets(df, dW, dws, stream=s_cmp)
+            mt.mt_components_at(df, dW, t_thr, dl, dws, stream=s_cmp)
+            built = torch.cuda.Event()
+            built.record(s_cmp)
+            s_out.wait_event(built)
+            with torch.cuda.stream(s_out):
+                h_W.copy_(dW, non_blocking=True)
+                h_lab.copy_(dl, non_blocking=True)
+            if not last:
+                prefetch(k + 1)  # the next field's upload overlaps this step
+            np_, _ = mt.mt_persistence_pairs(df, dW, dp, dws, stream=s_cmp)
+            paired = torch.cuda.Event()
+            paired.record(s_cmp)
+            s_out.wait_event(paired)
+            with torch.cuda.stream(s_out):
+                h_pairs[:np_].copy_(dp[:np_], non_blocking=True)
+                done[k % 2].record(s_out)
+
+        prefetch(0)
+        e2e_step(0, True)
+        torch.cuda.synchronize(dev)
         barrier()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(k_e2e):
-            e2e_step()
-        b.record(stream)
-        barrier()
-        e_ms = a.elapsed_time(b)
+        t0 = time.perf_counter()
+        prefetch(0)
+        for k in range(k_e2e):
+            e2e_step(k, k + 1 == k_e2e)
+        torch.cuda.synchronize(dev)
+        e_ms = (time.perf_counter() - t0) * 1e3
         if world > 1:
             import torch.distributed as dist
 
@@ -293,8 +325,9 @@ def run_ours(args):
             e_ms = float(tt.item())
         e2e = {"value": round(world * n * k_e2e / (e_ms / 1e3) / 1e6, 1), "unit": UNIT,
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n + 8 * npairs + 4 * n,
-               "ms_per_step": round(e_ms / k_e2e, 3), "steps": k_e2e}
-        del h_f, h_W, h_lab, h_pairs, d_f2
+               "ms_per_step": round(e_ms / k_e2e, 3), "steps": k_e2e,
+               "timing": "host wall clock around K pipelined steps (copies on their own streams), synchronised"}
+        del h_f, h_W, h_lab, h_pairs, bufs
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
