@@ -160,6 +160,24 @@ def traffic_record(kernel: str):
     return rec.get("dram_bytes_per_launch") if rec.get("mt_build_cu_sha256_16") == h else None
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The slowest rank's time (replicas: the job ends with the last one)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: int, steps: int, ms_total: float) -> float:
+    """Whole-job throughput in millions of units per second: every rank
+    processes its own units each step; the job time is the slowest rank's."""
+    return world * units_per_rank * steps / (ms_total / 1e3) / 1e6
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -236,15 +254,9 @@ def run_ours(args):
     phases = mt.mt_trace_read(reset=True)
     mt.mt_trace_enable(False)
     mt.mt_sync_status(ws)
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_step = ms_total / args.steps
-    value = world * n * args.steps / (ms_total / 1e3) / 1e6
+    value = job_rate(world, n, args.steps, ms_total)
 
     # roofline of the dominant kernel family from the live phase timing
     peak, peak_kind = measured_peaks()
@@ -316,14 +328,8 @@ def run_ours(args):
         for k in range(k_e2e):
             e2e_step(k, k + 1 == k_e2e)
         torch.cuda.synchronize(dev)
-        e_ms = (time.perf_counter() - t0) * 1e3
-        if world > 1:
-            import torch.distributed as dist
-
-            tt = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        e2e = {"value": round(world * n * k_e2e / (e_ms / 1e3) / 1e6, 1), "unit": UNIT,
+        e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, dev)
+        e2e = {"value": round(job_rate(world, n, k_e2e, e_ms), 1), "unit": UNIT,
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n + 8 * npairs + 4 * n,
                "ms_per_step": round(e_ms / k_e2e, 3), "steps": k_e2e,
                "timing": "host wall clock around K pipelined steps (copies on their own streams), synchronised"}

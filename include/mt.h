@@ -56,7 +56,7 @@ typedef struct {
 
 typedef int32_t mt_status;
 #define MT_OK 0
-#define MT_ERR_INVALID (-1)   /* null pointer, zero side, misaligned or short buffer */
+#define MT_ERR_INVALID (-1)   /* null pointer, zero side, misaligned or short buffer; caller triplets with ids >= n */
 #define MT_ERR_TOO_LARGE (-2) /* n >= 2^32 - 1 */
 #define MT_ERR_NONFINITE (-3) /* the field holds NaN or +-inf */
 #define MT_ERR_CAPACITY (-4)  /* an output buffer was too small; true count reported */
@@ -70,8 +70,10 @@ const char *mt_status_str(mt_status st);
 
 /* Bytes of device workspace that mt_build_triplets, mt_persistence_pairs and
  * mt_components_at need for grid g (0 if g is invalid). The workspace must be
- * 256-byte aligned; its contents need no initialisation and may be reused
- * from call to call on the same stream. */
+ * 256-byte aligned and may be reused from call to call on the same stream.
+ * Its first 256 bytes hold the status word: zero them once before the first
+ * use (mt_build_triplets clears them itself, and so does mt_sync_status);
+ * the rest needs no initialisation. */
 size_t mt_workspace_bytes(mt_grid g);
 
 /*
@@ -119,6 +121,9 @@ mt_status mt_persistence_pairs(const float *d_f, const uint64_t *d_W, mt_grid g,
  * at level t (Algorithm 4 with the value test f(s) <= t), i.e. the deepest
  * vertex of u's component, or 0xFFFFFFFF when f[u] > t. Asynchronous.
  *   d_labels  uint32[n], output.  t must not be NaN.
+ * d_W is followed from vertex to vertex: an id >= n in it sets the status
+ * word to MT_ERR_INVALID, and a chain longer than n (a cycle, impossible in
+ * a tree) to MT_ERR_TIMEOUT; neither reads outside the arrays.
  */
 mt_status mt_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t *d_labels,
                            void *d_ws, size_t ws_bytes, void *stream);

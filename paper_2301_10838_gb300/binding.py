@@ -183,11 +183,13 @@ def mt_workspace_bytes(grid: Grid) -> int:
 
 def workspace(grid: Grid, device=None) -> torch.Tensor:
     """A device byte tensor big enough for ``grid`` (torch allocations are
-    256-byte aligned)."""
+    256-byte aligned) with its status word cleared."""
     nbytes = mt_workspace_bytes(grid)
     if nbytes == 0:
         raise MtError(-1, "mt_workspace_bytes")
-    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+    ws[:256].zero_()
+    return ws
 
 
 def mt_build_triplets(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, stream=None) -> None:

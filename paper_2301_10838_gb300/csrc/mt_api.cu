@@ -69,6 +69,7 @@ mt_status status_from_bits(uint32_t bits)
     if (bits & ST_NONFINITE) return MT_ERR_NONFINITE;
     if (bits & ST_TIMEOUT) return MT_ERR_TIMEOUT;
     if (bits & ST_CAPACITY) return MT_ERR_CAPACITY;
+    if (bits & ST_CORRUPT) return MT_ERR_INVALID;
     return MT_OK;
 }
 

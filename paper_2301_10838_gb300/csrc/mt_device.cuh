@@ -14,6 +14,7 @@ enum : uint32_t {
     ST_NONFINITE = 1u,
     ST_TIMEOUT = 2u,
     ST_CAPACITY = 4u,
+    ST_CORRUPT = 8u,  // a triplet array given by the caller holds an id >= n
 };
 
 // Limits of the bounded device loops. A merge that needs more steps than this

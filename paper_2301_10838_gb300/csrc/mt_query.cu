@@ -14,29 +14,34 @@ namespace mt {
 
 // ------------------------------------------------------------------ pairs
 //
-// One CTA per chunk of kCompactChunk consecutive vertices of a field, read in
-// 16 rounds of 256 consecutive vertices so that every load is coalesced. A
-// pass counts the pairs of each chunk (and finds the roots), a scan per field
-// turns the counts into offsets, and a second pass writes each chunk's pairs
-// at its offset in order. Each round ranks its flags with warp ballots plus a
-// prefix over the 8 warp totals, which keeps the ascending order.
+// One CTA per chunk of kCompactChunk consecutive vertices of a field; warp w
+// owns the contiguous slice [w * 512, (w + 1) * 512) of the chunk and reads it
+// in 16 coalesced rows of 32. A pass counts the pairs of each chunk (and finds
+// the roots), a scan per field turns the counts into offsets, and a second
+// pass writes each chunk's pairs at its offset in order: every warp keeps its
+// 16 triplets in registers, ranks its flags with ballots, and one barrier
+// combines the 8 warp totals, which keeps the ascending order.
 constexpr int kCompactThreads = 256;
-constexpr int kCompactRounds = kCompactChunk / kCompactThreads;
+constexpr int kCompactWarps = kCompactThreads / 32;
+constexpr int kCompactRows = kCompactChunk / kCompactThreads;  // rows of 32 per warp
+static_assert(kCompactRows * 32 * kCompactWarps == kCompactChunk, "chunk = warps x rows x 32");
 
 template <class Loc>
 __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32_t *counts, const uint32_t *status)
 {
     if (*status) return;
-    __shared__ uint32_t warp_sum[kCompactThreads / 32];
+    __shared__ uint32_t warp_sum[kCompactWarps];
     uint64_t local;
     uint32_t fi;
     const FieldDesc fd = loc.chunk(blockIdx.x, local, fi);
     const uint64_t *__restrict__ W = fd.W;
     const uint64_t n = fd.n;
-    const uint64_t b0 = local * kCompactChunk;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t b0 = local * kCompactChunk + (uint64_t)warp * (kCompactRows * 32);
     uint32_t c = 0;
-    for (int r = 0; r < kCompactRounds; r++) {
-        const uint64_t u = b0 + (uint64_t)r * kCompactThreads + threadIdx.x;
+#pragma unroll 4
+    for (int r = 0; r < kCompactRows; r++) {
+        const uint64_t u = b0 + (uint64_t)r * 32 + lane;
         if (u >= n) break;
         const uint64_t T = W[u];
         if (tri_s(T) != (uint32_t)u) {
@@ -47,11 +52,11 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32
         }
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+    if (lane == 0) warp_sum[warp] = c;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t tot = 0;
-        for (int w = 0; w < kCompactThreads / 32; w++) tot += warp_sum[w];
+        for (int w = 0; w < kCompactWarps; w++) tot += warp_sum[w];
         counts[blockIdx.x] = tot;
     }
 }
@@ -98,43 +103,41 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const 
                                                                  const uint32_t *status)
 {
     if (*status) return;
-    __shared__ uint32_t warp_cnt[kCompactThreads / 32];
+    __shared__ uint32_t warp_cnt[kCompactWarps];
     uint64_t local;
     uint32_t fi;
     const FieldDesc fd = loc.chunk(blockIdx.x, local, fi);
     const uint64_t *__restrict__ W = fd.W;
     const uint64_t n = fd.n, cap = fd.cap;
     uint32_t *pairs = fd.pairs;
-    const uint64_t b0 = local * kCompactChunk;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t b0 = local * kCompactChunk + (uint64_t)warp * (kCompactRows * 32);
+    uint64_t Tr[kCompactRows];
+    uint32_t c = 0;
+#pragma unroll
+    for (int r = 0; r < kCompactRows; r++) {
+        const uint64_t u = b0 + (uint64_t)r * 32 + lane;
+        Tr[r] = u < n ? W[u] : tri_pack((uint32_t)u, (uint32_t)u);  // past the end: no pair
+        c += __popc(__ballot_sync(0xffffffffu, tri_s(Tr[r]) != (uint32_t)u));
+    }
+    if (lane == 0) warp_cnt[warp] = c;
+    __syncthreads();
     uint64_t run = offsets[blockIdx.x];
-    for (int r = 0; r < kCompactRounds; r++) {
-        const uint64_t u = b0 + (uint64_t)r * kCompactThreads + threadIdx.x;
-        if (b0 + (uint64_t)r * kCompactThreads >= n) break;  // uniform across the CTA
-        uint64_t T = 0;
-        bool flag = false;
-        if (u < n) {
-            T = W[u];
-            flag = tri_s(T) != (uint32_t)u;
-        }
+    for (uint32_t w = 0; w < warp; w++) run += warp_cnt[w];
+    const uint32_t below = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kCompactRows; r++) {
+        const uint64_t u = b0 + (uint64_t)r * 32 + lane;
+        const bool flag = tri_s(Tr[r]) != (uint32_t)u;
         const uint32_t ball = __ballot_sync(0xffffffffu, flag);
-        if (lane == 0) warp_cnt[warp] = __popc(ball);
-        __syncthreads();
-        uint32_t before_w = 0, total = 0;
-        for (int w = 0; w < kCompactThreads / 32; w++) {
-            const uint32_t c = warp_cnt[w];
-            before_w += w < warp ? c : 0;
-            total += c;
-        }
         if (flag) {
-            const uint64_t pos = run + before_w + __popc(ball & ((1u << lane) - 1u));
+            const uint64_t pos = run + __popc(ball & below);
             if (pos < cap) {
                 pairs[2 * pos] = (uint32_t)u;
-                pairs[2 * pos + 1] = tri_s(T);
+                pairs[2 * pos + 1] = tri_s(Tr[r]);
             }
         }
-        run += total;
-        __syncthreads();
+        run += __popc(ball);
     }
 }
 
@@ -191,6 +194,9 @@ __global__ void __launch_bounds__(512) k_labels(const Field f, const uint64_t *_
                                                 uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty, float t,
                                                 uint32_t *__restrict__ labels, uint32_t *status)
 {
+    const uint32_t n = nx * ny * nz;
+    const uint32_t limit = n < kChaseLimit ? n : kChaseLimit;
+    bool bad = false;
     if (*status) return;
     constexpr uint32_t TX = 1u << kLabLX, TY = 1u << kLabLY, TZ = 1u << kLabLZ, TV = TX * TY * TZ;
     const uint32_t tile = blockIdx.x;
@@ -206,13 +212,21 @@ __global__ void __launch_bounds__(512) k_labels(const Field f, const uint64_t *_
         const uint32_t u = base + lz * nxy + ly * nx + lx;
         uint32_t lab = 0xFFFFFFFFu;
         if (f[u] <= t) {
+            // the caller's triplets are followed only through ids < n, and
+            // for at most `limit` links: a chain of a valid tree is shorter
+            // than n, so a longer one means a cycle
             uint32_t x = u;
             for (uint32_t h = 0;; h++) {
                 const uint64_t T = __ldg(reinterpret_cast<const unsigned long long *>(W) + x);
                 const uint32_t s = tri_s(T);
-                if (T == tri_pack(x, x) || !(f[s] <= t)) break;
+                if (T == tri_pack(x, x)) break;
+                if (s >= n || tri_v(T) >= n) {
+                    bad = true;
+                    break;
+                }
+                if (!(f[s] <= t)) break;
                 x = tri_v(T);
-                if (h > kChaseLimit) {
+                if (h >= limit) {
                     ok = false;
                     break;
                 }
@@ -222,6 +236,7 @@ __global__ void __launch_bounds__(512) k_labels(const Field f, const uint64_t *_
         labels[u] = lab;
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
+    if (bad) raise_status(status, ST_CORRUPT);
 }
 
 cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, float t,

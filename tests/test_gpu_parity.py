@@ -250,3 +250,32 @@ def test_full_size_lognormal_1024():
             assert flat[L] <= t and int(lab_np[L]) == L
         else:
             assert lab_np[u] == 0xFFFFFFFF
+
+
+def test_corrupt_triplets_are_reported_not_followed():
+    """Labels follow the caller's triplets: out-of-range ids and cycles are
+    reported through the status word, without reads outside the arrays."""
+    f = torch.from_numpy(fields.white_noise((10, 10, 10), 3)).cuda()
+    n = f.numel()
+    ws = mt.workspace(mt.grid_of(f))
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    # every vertex points at vertex 0 below it, and vertex 0 points at n + 5
+    W = (torch.arange(n, dtype=torch.int64, device="cuda") << 32)
+    W[0] = n + 5
+    mt.mt_components_at(f, W, 2.0, lab, ws)
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_sync_status(ws)
+    assert e.value.code == -1
+    # a two-cycle: 1 -> 2 -> 1 with saddles inside G_t
+    W = torch.arange(n, dtype=torch.int64, device="cuda") * ((1 << 32) + 1)  # all roots
+    W[1] = (1 << 32) | 2
+    W[2] = (2 << 32) | 1
+    mt.mt_components_at(f, W, 2.0, lab, ws)
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_sync_status(ws)
+    assert e.value.code == -7
+    # the workspace stays usable
+    W_ok = torch.from_numpy(oracle.merge_tree(f.cpu().numpy()).view(np.int64)).cuda()
+    mt.mt_components_at(f, W_ok, 0.5, lab, ws)
+    mt.mt_sync_status(ws)
+    assert np.array_equal(lab.cpu().numpy().view(np.uint32), oracle.components(f.cpu().numpy(), 0.5))
