@@ -161,7 +161,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     uint32_t *hist = queue;                                       // key histogram (before the rounds)
     __shared__ uint8_t s_bmap[BINS];                              // histogram bin -> bucket
     __shared__ uint32_t s_kmin, s_kmax, s_nvalid, s_qlen, s_warp[NT / 32];
-    __shared__ uint32_t s_boff[NB + 1], s_bcur[NB];
+    __shared__ uint32_t s_boff[NB + 2], s_bcur[NB + 1];
 
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
@@ -181,7 +181,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
         s_kmin = 0xFFFFFFFFu, s_kmax = 0, s_qlen = 0;
         s_nvalid = wx * wy * wz;
     }
-    if (threadIdx.x < NB) s_bcur[threadIdx.x] = 0;
+    if (threadIdx.x <= NB) s_bcur[threadIdx.x] = 0;
     for (uint32_t i = threadIdx.x; i < (uint32_t)BINS; i += NT) hist[i] = 0;
     __syncthreads();
 
@@ -282,26 +282,65 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
                 (uint8_t)min((uint32_t)NB - 1, (uint32_t)(((uint64_t)(before_w + incl - c) * NB) / s_nvalid));
     }
     __syncthreads();
+    volatile uint32_t *vT = T;
     auto bucket_of = [&](uint32_t k) { return (uint32_t)s_bmap[bin_of(k)]; };
+    // Spare bits of an inner vertex's triplet (ids take IDB of each 16-bit
+    // half) carry its cross mask: bit d is set when its neighbour in direction
+    // d (-x, -y, -z, +x, +y, +z) is lower and descends to another minimum.
+    // Only those edges can join two components; the scan of the vertex's
+    // level bucket reads them from here. The bucket repair of the vertex
+    // rewrites its triplet and so clears the bits; minima never carry any.
+    auto tid_s = [](uint32_t w) { return (w >> 16) & IDM; };
+    auto tid_v = [](uint32_t w) { return w & IDM; };
+    auto xmask = [](uint32_t w) { return ((w >> IDB) & 7u) | (((w >> (16 + IDB)) & 7u) << 3); };
+    auto nbr = [](uint32_t l, uint32_t d) -> uint32_t {
+        const uint32_t a = d < 3 ? d : d - 3;
+        const uint32_t step = 1u << (a == 0 ? 0 : a == 1 ? LX : LX + LY);
+        return d < 3 ? l - step : l + step;
+    };
 
-    // 4. counting sort of the vertices by bucket
-    for (uint32_t l = threadIdx.x; l < TV; l += NT)
-        if (valid(l)) atomicAdd(&s_bcur[bucket_of(K[l])], 1u);
+    // 4. cross masks, then a counting sort of the vertices by segment:
+    //    inner vertices by level bucket (segments 0 .. NB-1), minima last
+    //    (segment NB)
+    for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+        if (!valid(l)) continue;
+        const uint32_t w0 = vT[l];
+        const uint32_t dl = sm_v(w0);
+        if (dl == l) {  // a minimum
+            atomicAdd(&s_bcur[NB], 1u);
+            continue;
+        }
+        const uint32_t lx = lxo(l), ly = lyo(l), lz = lzo(l), kl = K[l];
+        uint32_t m = 0;
+#pragma unroll
+        for (uint32_t d = 0; d < 6; d++) {
+            const bool in = d == 0 ? lx > 0 : d == 1 ? ly > 0 : d == 2 ? lz > 0 :
+                            d == 3 ? lx + 1 < wx : d == 4 ? ly + 1 < wy : lz + 1 < wz;
+            if (!in) continue;
+            const uint32_t w = nbr(l, d);
+            if (!kbefore(K[w], w, kl, l)) continue;
+            const uint32_t Tw = vT[w];
+            const uint32_t dw = tid_v(Tw) == w ? w : tid_v(Tw);  // w's minimum
+            if (dw != dl) m |= 1u << d;
+        }
+        atomicAdd(&s_bcur[bucket_of(kl)], 1u);
+        vT[l] = sm_pack(l, dl) | ((m & 7u) << IDB) | ((m >> 3) << (16 + IDB));
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t run = 0;
-        for (int b = 0; b < NB; b++) {
+        for (int b = 0; b <= NB; b++) {
             s_boff[b] = run;
             run += s_bcur[b];
             s_bcur[b] = s_boff[b];
         }
-        s_boff[NB] = run;
+        s_boff[NB + 1] = run;
     }
     __syncthreads();
     for (uint32_t l0 = 0; l0 < TV; l0 += NT) {
         const uint32_t l = l0 + threadIdx.x;
         const bool ok_l = valid(l);
-        const uint32_t b = ok_l ? bucket_of(K[l]) : 0xFFFFFFFFu;
+        const uint32_t b = !ok_l ? 0xFFFFFFFFu : tid_v(vT[l]) == l ? (uint32_t)NB : bucket_of(K[l]);
         const uint32_t peers = __match_any_sync(0xffffffffu, b);
         if (ok_l) {
             const uint32_t leader = __ffs(peers) - 1;
@@ -315,7 +354,6 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
 
     // 5. rounds over the level buckets
     bool ok = true;
-    volatile uint32_t *vT = T;
     volatile uint16_t *vSC = SC;
     for (int b = 0; b < NB; b++) {
         // shortcut of minimum m for round b: climb through the links whose
@@ -333,36 +371,28 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
             return x;
         };
         const uint32_t i0 = s_boff[b], i1 = s_boff[b + 1];
-        // 5a. scan the edges whose upper end S lies in bucket b; queue those
-        //     whose ends are not yet known to be connected below S
+        // 5a. scan the cross edges whose upper end S lies in bucket b; queue
+        //     those whose ends are not yet known to be connected below S
         for (uint32_t i = i0 + threadIdx.x; i < i1; i += NT) {
             const uint32_t S = vlist[i];
             const uint32_t TSw = vT[S];
-            if (sm_s(TSw) != S || sm_v(TSw) == S) continue;  // a minimum has no lower neighbour
-            const uint32_t kS = K[S], dS = sm_v(TSw);
-            const uint32_t lx = lxo(S), ly = lyo(S), lz = lzo(S);
-            uint32_t aS = 0xFFFFFFFFu;
-#pragma unroll
-            for (int d = 0; d < 6; d++) {
-                uint32_t w;
-                if (d == 0) { if (lz == 0) continue; w = S - TX * TY; }
-                else if (d == 1) { if (ly == 0) continue; w = S - TX; }
-                else if (d == 2) { if (lx == 0) continue; w = S - 1; }
-                else if (d == 3) { if (lx + 1 >= wx) continue; w = S + 1; }
-                else if (d == 4) { if (ly + 1 >= wy) continue; w = S + TX; }
-                else { if (lz + 1 >= wz) continue; w = S + TX * TY; }
-                if (!kbefore(K[w], w, kS, S)) continue;  // only edges to lower neighbours
+            uint32_t m = xmask(TSw);
+            if (m == 0) continue;
+            const uint32_t kS = K[S];
+            const uint32_t aS = shortcut(tid_v(TSw));
+            do {
+                const uint32_t d = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t w = nbr(S, d);
                 const uint32_t Tw = vT[w];
                 // w's minimum: an inner vertex's target, else w itself
-                const uint32_t dw = (sm_s(Tw) == w && sm_v(Tw) != w) ? sm_v(Tw) : w;
-                if (dw == dS) continue;
-                if (aS == 0xFFFFFFFFu) aS = shortcut(dS);
+                const uint32_t dw = (tid_s(Tw) == w && tid_v(Tw) != w) ? tid_v(Tw) : w;
                 const uint32_t aw = shortcut(dw);
                 if (aw == aS) continue;  // already connected below S
                 const uint32_t slot = atomicAdd(&s_qlen, 1u);
                 if (slot < (uint32_t)Q) queue[slot] = (S << 16) | aw;
                 else sm_merge<TV>(T, K, S, kS, aS, aw, ok);  // queue full: merge in place
-            }
+            } while (m);
         }
         __syncthreads();
         // 5b. run the queued merges side by side
@@ -371,27 +401,26 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
             for (uint32_t i = threadIdx.x; i < nq; i += NT) {
                 const uint32_t e = queue[i];
                 const uint32_t S = e >> 16, c = e & 0xFFFFu;
-                const uint32_t aS = vSC[sm_v(vT[S])] & IDM;  // set in 5a for this round
+                const uint32_t aS = vSC[tid_v(vT[S])] & IDM;  // set in 5a for this round
                 sm_merge<TV>(T, K, S, K[S], aS, c, ok);
             }
         }
         __syncthreads();
         if (threadIdx.x == 0) s_qlen = 0;
-        // 5c. final tile triplets of the inner vertices of bucket b
+        // 5c. final tile triplets of the inner vertices of bucket b (this
+        //     also clears their cross masks)
         for (uint32_t i = i0 + threadIdx.x; i < i1; i += NT) {
             const uint32_t l = vlist[i];
-            const uint32_t w = vT[l];
-            if (sm_s(w) != l || sm_v(w) == l) continue;
             uint32_t wr;
-            const uint32_t r = sm_climb<TV>(T, K, shortcut(sm_v(w)), l, K[l], wr, ok);
-            if (r != sm_v(w)) T[l] = sm_pack(l, r);
+            const uint32_t r = sm_climb<TV>(T, K, shortcut(tid_v(vT[l])), l, K[l], wr, ok);
+            T[l] = sm_pack(l, r);
         }
         __syncthreads();
     }
 
     // 6. repair the branch minima (Algorithm 5)
-    for (uint32_t l = threadIdx.x; l < TV; l += NT) {
-        if (!valid(l)) continue;
+    for (uint32_t i = s_boff[NB] + threadIdx.x; i < s_boff[NB + 1]; i += NT) {
+        const uint32_t l = vlist[i];
         const uint32_t w = vT[l];
         const uint32_t s = sm_s(w);
         if (s == l) continue;  // inner vertex or root
