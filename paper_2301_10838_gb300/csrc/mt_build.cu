@@ -45,8 +45,13 @@ namespace mt {
 // and SC[c] (both joined to a, c below S), and when they coincide the ends are
 // already connected below S and the edge is settled by two shared-memory
 // loads, as about nine edges in ten are on these fields. The others are
-// queued and merged together once the bucket's scan is done, so that the
+// collected and merged together once the bucket's scan is done, so that the
 // lanes of a warp run their merges side by side instead of one after another.
+// They are collected in a shared-memory hash keyed by the pair of shortcuts
+// that keeps, per pair, only the edge with the earliest upper end: once that
+// one is merged, the two components are joined below the level of every
+// other edge of the pair, which Merge would then find connected and skip. On
+// these fields about two collected edges in five repeat a pair.
 //
 // Repair. Right after round b no later merge can change a component below
 // the levels of bucket b, so every inner vertex l of bucket b gets its final
@@ -57,6 +62,8 @@ namespace mt {
 // What leaves the kernel is, for every vertex, its triplet in the subgraph
 // induced by its tile: a valid normalised triplet tree of the full grid minus
 // the edges between tiles, which k_cross merges next.
+constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
+
 template <int LX, int LY, int LZ, int NT = 512>
 struct Tile {
     static constexpr int TX = 1 << LX, TY = 1 << LY, TZ = 1 << LZ;
@@ -64,11 +71,14 @@ struct Tile {
     static_assert(TV <= 65536, "local ids are 16-bit");
     static_assert(TX % 4 == 0, "rows are loaded as float4");
     static constexpr int kBins = NT;     // key histogram, one bin per thread
-    static constexpr int kQueue = 2048 * TV / 8192 > NT ? 2048 * TV / 8192 : NT;  // deferred merges per flush
+    static constexpr int kQueue = 2048 * TV / 8192 > NT ? 2048 * TV / 8192 : NT;  // 32-bit words of the edge hash
+    static constexpr int kHashLog = log2i(kQueue / 3);                            // slots: 32-bit pair + 64-bit level
+    static constexpr int kHash = 1 << kHashLog;
+    static_assert(kHash * 12 <= kQueue * 4, "hash fits its buffer");
     // shared memory: keys + triplets (4 B each), shortcuts + bucket-sorted
-    // vertex list (2 B each), merge queue (aliased by the key histogram)
+    // vertex list (2 B each), edge hash (aliased by the key histogram)
     static constexpr size_t kSmem = (size_t)TV * (4 + 4 + 2 + 2) + (size_t)kQueue * 4;
-    static_assert(kQueue >= kBins, "the histogram lives in the queue buffer");
+    static_assert(kQueue >= kBins, "the histogram lives in the hash buffer");
 };
 
 __device__ __forceinline__ uint32_t sm_pack(uint32_t s, uint32_t v) { return (s << 16) | v; }
@@ -147,7 +157,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     const uint32_t nx = fd.nx, ny = fd.ny, nz = fd.nz, ntx = fd.ntx, nty = fd.nty;
     const bool vec = (nx % 4 == 0) && ((uintptr_t)f % 16 == 0) && ((uintptr_t)W % 16 == 0);
     using TS = Tile<LX, LY, LZ, NT>;
-    constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV, BINS = TS::kBins, Q = TS::kQueue;
+    constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV, BINS = TS::kBins, HS = TS::kHash, HLOG = TS::kHashLog;
     constexpr uint32_t IDB = LX + LY + LZ;  // bits of a local id
     constexpr uint32_t IDM = (1u << IDB) - 1u;
     static_assert(NT >= BINS, "one histogram bin per thread");
@@ -157,10 +167,13 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     uint32_t *T = smem + TV;                                      // triplets (s << 16) | v
     uint16_t *SC = reinterpret_cast<uint16_t *>(smem + 2 * TV);   // shortcuts (round << IDB) | vertex
     uint16_t *vlist = SC + TV;                                    // vertices sorted by bucket
-    uint32_t *queue = reinterpret_cast<uint32_t *>(vlist + TV);   // deferred merges (S << 16) | c
-    uint32_t *hist = queue;                                       // key histogram (before the rounds)
+    // edges to merge in the current round, one per pair of shortcuts:
+    // hkey = (lo << IDB) | hi, hlev = (key << 32) | S of the earliest upper end
+    unsigned long long *hlev = reinterpret_cast<unsigned long long *>(vlist + TV);
+    uint32_t *hkey = reinterpret_cast<uint32_t *>(hlev + HS);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(hlev);          // key histogram (before the rounds)
     __shared__ uint8_t s_bmap[BINS];                              // histogram bin -> bucket
-    __shared__ uint32_t s_kmin, s_kmax, s_nvalid, s_qlen, s_warp[NT / 32];
+    __shared__ uint32_t s_kmin, s_kmax, s_nvalid, s_warp[NT / 32];
     __shared__ uint32_t s_boff[NB + 2], s_bcur[NB + 1];
 
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -178,7 +191,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     auto valid = [&](uint32_t l) { return FULL || (lxo(l) < wx && lyo(l) < wy && lzo(l) < wz); };
     auto gid = [&](uint32_t l) { return base + lzo(l) * nxy + lyo(l) * nx + lxo(l); };
     if (threadIdx.x == 0) {
-        s_kmin = 0xFFFFFFFFu, s_kmax = 0, s_qlen = 0;
+        s_kmin = 0xFFFFFFFFu, s_kmax = 0;
         s_nvalid = wx * wy * wz;
     }
     if (threadIdx.x <= NB) s_bcur[threadIdx.x] = 0;
@@ -301,7 +314,8 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
 
     // 4. cross masks, then a counting sort of the vertices by segment:
     //    inner vertices by level bucket (segments 0 .. NB-1), minima last
-    //    (segment NB)
+    //    (segment NB); the histogram is consumed, so the edge hash is cleared
+    for (uint32_t i = threadIdx.x; i < (uint32_t)HS; i += NT) hkey[i] = 0xFFFFFFFFu, hlev[i] = ~0ull;
     for (uint32_t l = threadIdx.x; l < TV; l += NT) {
         if (!valid(l)) continue;
         const uint32_t w0 = vT[l];
@@ -355,6 +369,8 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     // 5. rounds over the level buckets
     bool ok = true;
     volatile uint16_t *vSC = SC;
+    volatile uint32_t *vHK = hkey;
+    volatile unsigned long long *vHL = hlev;
     for (int b = 0; b < NB; b++) {
         // shortcut of minimum m for round b: climb through the links whose
         // saddle lies in an earlier bucket, from where round (SC >> IDB) left it
@@ -371,8 +387,9 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
             return x;
         };
         const uint32_t i0 = s_boff[b], i1 = s_boff[b + 1];
-        // 5a. scan the cross edges whose upper end S lies in bucket b; queue
-        //     those whose ends are not yet known to be connected below S
+        // 5a. scan the cross edges whose upper end S lies in bucket b; collect
+        //     those whose ends are not yet known to be connected below S,
+        //     one per pair of shortcuts (the earliest S)
         for (uint32_t i = i0 + threadIdx.x; i < i1; i += NT) {
             const uint32_t S = vlist[i];
             const uint32_t TSw = vT[S];
@@ -389,24 +406,33 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
                 const uint32_t dw = (tid_s(Tw) == w && tid_v(Tw) != w) ? tid_v(Tw) : w;
                 const uint32_t aw = shortcut(dw);
                 if (aw == aS) continue;  // already connected below S
-                const uint32_t slot = atomicAdd(&s_qlen, 1u);
-                if (slot < (uint32_t)Q) queue[slot] = (S << 16) | aw;
-                else sm_merge<TV>(T, K, S, kS, aS, aw, ok);  // queue full: merge in place
+                const uint32_t pr = aS < aw ? (aS << IDB) | aw : (aw << IDB) | aS;
+                const unsigned long long lev = ((unsigned long long)kS << 32) | S;
+                uint32_t h = (pr * 0x9E3779B1u) >> (32 - HLOG);
+                bool placed = false;
+                for (uint32_t p = 0; p < 16; p++) {
+                    uint32_t k0 = vHK[h];
+                    if (k0 == 0xFFFFFFFFu) k0 = atomicCAS(hkey + h, 0xFFFFFFFFu, pr);
+                    if (k0 == 0xFFFFFFFFu || k0 == pr) {  // the pair's slot: keep the earliest level
+                        if (vHL[h] > lev) atomicMin(hlev + h, lev);
+                        placed = true;
+                        break;
+                    }
+                    h = (h + 1) & (HS - 1);
+                }
+                if (!placed) sm_merge<TV>(T, K, S, kS, aS, aw, ok);  // hash crowded: merge in place
             } while (m);
         }
         __syncthreads();
-        // 5b. run the queued merges side by side
-        {
-            const uint32_t nq = min(s_qlen, (uint32_t)Q);
-            for (uint32_t i = threadIdx.x; i < nq; i += NT) {
-                const uint32_t e = queue[i];
-                const uint32_t S = e >> 16, c = e & 0xFFFFu;
-                const uint32_t aS = vSC[tid_v(vT[S])] & IDM;  // set in 5a for this round
-                sm_merge<TV>(T, K, S, K[S], aS, c, ok);
-            }
+        // 5b. run the collected merges side by side and clear the hash
+        for (uint32_t i = threadIdx.x; i < (uint32_t)HS; i += NT) {
+            const uint32_t pr = hkey[i];
+            if (pr == 0xFFFFFFFFu) continue;
+            const unsigned long long lev = hlev[i];
+            hkey[i] = 0xFFFFFFFFu, hlev[i] = ~0ull;
+            sm_merge<TV>(T, K, (uint32_t)lev, (uint32_t)(lev >> 32), pr >> IDB, pr & IDM, ok);
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_qlen = 0;
         // 5c. final tile triplets of the inner vertices of bucket b (this
         //     also clears their cross masks)
         for (uint32_t i = i0 + threadIdx.x; i < i1; i += NT) {
@@ -612,47 +638,241 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
 // Repair (Algorithm 5) after the cross-tile merges: T[u] = (s, Rep(u, s))
 // restores minimality. Level comparisons use the vertex order, not values
 // alone: with tied values a saddle s' equal in value to s but after it in the
-// order is not yet part of the sublevel set at s. One CTA per tile: first the
-// tile's branch minima (s != u), then, after a barrier, its inner vertices
-// (s == u != v), whose chases start at the tile's (now repaired) minima and
-// so mostly hit L1. Concurrent repairs only replace a target by one further
-// along the same chain below the same level, so a stale cached copy of an
-// entry is still a valid (longer) way to the same answer: the chases use
-// ordinary L1-cached loads.
+// order is not yet part of the sublevel set at s. Concurrent repairs only
+// replace a target by one further along the same chain below the same level,
+// so a stale copy of an entry is still a valid (longer) way to the same
+// answer: every chase here uses ordinary cached loads.
+//
+// One CTA per tile, in four steps:
+//  1. scan the tile: collect its branch minima (s != u) in a list, and enter
+//     the target v of every inner vertex (s == u != v) in a shared-memory
+//     hash of targets (about 360 distinct targets serve the 7,400 inner
+//     vertices of a tile on the 1024^3 lognormal field);
+//  2. give each hashed target a slot for a copy of its chain;
+//  3. repair the branch minima, and copy the first kHops links of the chain
+//     of every hashed target into its slot, with the order keys of their
+//     saddles (one loop over both kinds of work, all lanes busy). A link
+//     whose saddle is not above the one before is folded into it (whoever
+//     passed the earlier saddle passes this one too), so the saddles of a
+//     copy increase strictly;
+//  4. repair every inner vertex: a binary search in its target's copy finds
+//     the last link at or below it, and only when the whole copy lies below
+//     it does the walk go on along the global chain.
+// Steps 1 and 4 load four rows per thread before using any, so that the
+// loads of a thread overlap. A branch minimum that finds the list full is
+// repaired on the spot in step 1; a target without a slot (hash or copies
+// full) is chased along the global chain in step 4.
+template <int LX, int LY, int LZ>
+struct RepairShape {
+    static constexpr uint32_t TV = 1u << (LX + LY + LZ);
+    static constexpr uint32_t kHops = 8;          // links copied per target
+    static constexpr uint32_t kCap = TV / 16;     // copies
+    static constexpr uint32_t kHash = TV / 8;     // hash slots for targets
+    static constexpr uint32_t kList = TV / 4;     // branch minima listed
+    static constexpr size_t kSmem =
+        (size_t)kCap * kHops * 12 + (size_t)kHash * 4 + (size_t)kHash * 2 + (size_t)kList * 2;
+};
+
 template <int LX, int LY, int LZ, int NT, class Loc>
-__global__ void __launch_bounds__(NT) k_repair(Loc loc, uint32_t *status)
+__global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
 {
     if (*status) return;
-    using TS = Tile<LX, LY, LZ>;
-    constexpr uint32_t TX = TS::TX, TY = TS::TY, TZ = TS::TZ, TV = TS::TV;
+    using RS = RepairShape<LX, LY, LZ>;
+    constexpr uint32_t TX = 1u << LX, TY = 1u << LY, TV = RS::TV, H = RS::kHops, CAP = RS::kCap,
+                       HS = RS::kHash, LIST = RS::kList;
+    constexpr uint32_t NB = 4;  // rows loaded together
+    static_assert(TV % (NT * NB) == 0, "whole batches of rows");
+    static_assert((H & (H - 1)) == 0 && (HS & (HS - 1)) == 0, "powers of two");
+    constexpr uint32_t EMPTY = 0xFFFFFFFFu;  // free hash slot (not a vertex id: ids are < n < 2^32 - 1)
+    constexpr uint32_t END = 0xFFFFFFFFu;    // copied saddle after the chain's root: above every (key, id)
+    constexpr uint16_t NOSLOT = 0xFFFFu;
+    constexpr uint32_t kProbes = 16;
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *es = smem;                       // copied links: saddle, its key, target
+    uint32_t *ek = es + CAP * H;
+    uint32_t *ev = ek + CAP * H;
+    uint32_t *hkey = ev + CAP * H;             // hashed targets
+    uint16_t *hslot = reinterpret_cast<uint16_t *>(hkey + HS);  // their copy slots
+    uint16_t *list = hslot + HS;               // branch minima (tile-local ids)
+    __shared__ uint32_t s_nmin, s_ncopy;
+
     uint32_t tile;
     const FieldDesc fd = loc.tile(blockIdx.x, tile);
     uint64_t *W = fd.W;
     const Field f{fd.f, fd.sg};
     const uint32_t nx = fd.nx, ny = fd.ny, nz = fd.nz, ntx = fd.ntx, nty = fd.nty;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-    const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
-    const uint32_t wx = min(TX, nx - x0), wy = min(TY, ny - y0), wz = min(TZ, nz - z0);
+    const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * (1u << LZ);
+    const uint32_t wx = min(TX, nx - x0), wy = min(TY, ny - y0), wz = min(1u << LZ, nz - z0);
     const uint32_t nxy = nx * ny;
     const uint32_t base = z0 * nxy + y0 * nx + x0;
+    const uint32_t lane = threadIdx.x & 31;
+    auto gid_of = [&](uint32_t l) {
+        return base + (l >> (LX + LY)) * nxy + ((l >> LX) & (TY - 1)) * nx + (l & (TX - 1));
+    };
+    auto inside = [&](uint32_t l) {
+        return (l & (TX - 1)) < wx && ((l >> LX) & (TY - 1)) < wy && (l >> (LX + LY)) < wz;
+    };
+    auto hash0 = [](uint32_t v) { return (v * 0x9E3779B1u) >> (32 - log2i(HS)); };
+    // slot of target v in the hash, HS if absent
+    auto find = [&](uint32_t v) -> uint32_t {
+        uint32_t h = hash0(v);
+        for (uint32_t p = 0; p < kProbes; p++) {
+            const uint32_t k = hkey[h];
+            if (k == v) return h;
+            if (k == EMPTY) return HS;
+            h = (h + 1) & (HS - 1);
+        }
+        return HS;
+    };
+
+    for (uint32_t i = threadIdx.x; i < HS; i += NT) hkey[i] = EMPTY;
+    if (threadIdx.x == 0) s_nmin = 0, s_ncopy = 0;
+    __syncthreads();
+
+    // 1. scan
     bool ok = true;
-    for (int pass = 0; pass < 2; pass++) {
-        for (uint32_t l = threadIdx.x; l < TV; l += NT) {
-            const uint32_t lx = l & (TX - 1), ly = (l >> LX) & (TY - 1), lz = l >> (LX + LY);
-            if (lx >= wx || ly >= wy || lz >= wz) continue;
-            const uint32_t u = base + lz * nxy + ly * nx + lx;
+    volatile uint32_t *vhk = hkey;
+    for (uint32_t l0 = 0; l0 < TV; l0 += NT * NB) {
+        uint64_t Tb[NB];
+#pragma unroll
+        for (uint32_t k = 0; k < NB; k++) {
+            const uint32_t l = l0 + k * NT + threadIdx.x;
+            const uint32_t u = gid_of(l);
+            Tb[k] = inside(l) ? W[u] : tri_pack(u, u);
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < NB; k++) {
+            const uint32_t l = l0 + k * NT + threadIdx.x;
+            const uint32_t u = gid_of(l);
+            const uint32_t s = tri_s(Tb[k]), v = tri_v(Tb[k]);
+            const bool is_min = s != u;
+            if (!is_min && v != u) {  // inner vertex: hash its target
+                uint32_t h = hash0(v);
+                for (uint32_t p = 0; p < kProbes; p++) {
+                    uint32_t kk = vhk[h];
+                    if (kk == EMPTY) kk = atomicCAS(hkey + h, EMPTY, v);
+                    if (kk == EMPTY || kk == v) break;
+                    h = (h + 1) & (HS - 1);
+                }
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, is_min);
+            if (bal) {
+                uint32_t pos = 0;
+                if (lane == 0) pos = atomicAdd(&s_nmin, __popc(bal));
+                pos = __shfl_sync(0xffffffffu, pos, 0) + __popc(bal & ((1u << lane) - 1u));
+                if (is_min && pos < LIST) {
+                    list[pos] = (uint16_t)l;
+                } else if (is_min) {  // list full: repair this branch minimum now
+                    uint32_t steps = 0;
+                    const uint32_t r = representative_cached(W, f, v, s, f[s], steps);
+                    if (steps > kChaseLimit) ok = false;
+                    else if (r != v) st_tri(W + u, tri_pack(s, r));
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // 2. copy slots for the hashed targets
+    for (uint32_t i = threadIdx.x; i < HS; i += NT) {
+        if (hkey[i] == EMPTY) continue;
+        const uint32_t c = atomicAdd(&s_ncopy, 1u);
+        hslot[i] = c < CAP ? (uint16_t)c : NOSLOT;
+    }
+    __syncthreads();
+
+    // 3. branch minima (items below nmin) and copies of target chains (one
+    //    item per hash slot)
+    const uint32_t nmin = min(s_nmin, LIST);
+    for (uint32_t i = threadIdx.x; i < nmin + HS; i += NT) {
+        if (i < nmin) {
+            const uint32_t u = gid_of(list[i]);
             const uint64_t T = W[u];
             const uint32_t s = tri_s(T), t = tri_v(T);
-            if (pass == 0 ? (s == u) : (s != u || t == u)) continue;
             uint32_t steps = 0;
             const uint32_t r = representative_cached(W, f, t, s, f[s], steps);
-            if (steps > kChaseLimit) {
-                ok = false;
-                continue;
-            }
-            if (r != t) st_tri(W + u, tri_pack(s, r));
+            if (steps > kChaseLimit) ok = false;
+            else if (r != t) st_tri(W + u, tri_pack(s, r));
+            continue;
         }
-        __syncthreads();
+        const uint32_t h = i - nmin;
+        const uint32_t x0v = hkey[h];
+        if (x0v == EMPTY || hslot[h] == NOSLOT) continue;
+        const uint32_t b = (uint32_t)hslot[h] * H;
+        uint32_t x = x0v, j = 0;
+        bool ended = false;
+        uint64_t T = W[x];
+        for (uint32_t step = 0; step < 4 * H && j < H; step++) {
+            const uint32_t s = tri_s(T), v = tri_v(T);
+            if (s == x && v == x) {  // a root: the chain ends
+                ended = true;
+                break;
+            }
+            const float fs = f[s];
+            const uint64_t Tn = W[v];  // loaded together with the saddle's value
+            const uint32_t ks = order_key(fs);
+            if (j > 0 && !kbefore(ek[b + j - 1], es[b + j - 1], ks, s)) {
+                ev[b + j - 1] = v;  // not above the previous saddle: fold
+            } else {
+                es[b + j] = s, ek[b + j] = ks, ev[b + j] = v;
+                j++;
+            }
+            x = v;
+            T = Tn;
+        }
+        // pad: after a root with END (above every level); when the copy
+        // stops short of the root, with the last link again, leading to x
+        // where a vertex above it goes on along the global chain
+        const uint32_t ps = ended ? END : es[b + j - 1], pk = ended ? END : ek[b + j - 1];
+        for (; j < H; j++) es[b + j] = ps, ek[b + j] = pk, ev[b + j] = x;
+    }
+    __syncthreads();
+
+    // 4. inner vertices
+    for (uint32_t l0 = 0; l0 < TV; l0 += NT * NB) {
+        uint64_t Tb[NB];
+        float fb[NB];
+#pragma unroll
+        for (uint32_t k = 0; k < NB; k++) {
+            const uint32_t l = l0 + k * NT + threadIdx.x;
+            const uint32_t u = gid_of(l);
+            const bool in = inside(l);
+            Tb[k] = in ? W[u] : tri_pack(u, u);
+            fb[k] = in ? f[u] : 0.0f;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < NB; k++) {
+            const uint32_t l = l0 + k * NT + threadIdx.x;
+            const uint32_t u = gid_of(l);
+            const uint32_t s = tri_s(Tb[k]), t = tri_v(Tb[k]);
+            if (s != u || t == u) continue;
+            const uint32_t h = find(t);
+            const uint16_t c = h < HS ? hslot[h] : NOSLOT;
+            uint32_t r = t;
+            bool global = true;
+            if (c != NOSLOT) {
+                const uint32_t b = (uint32_t)c * H;
+                const uint32_t ku = order_key(fb[k]);
+                // number of copied links at or below u (saddles increase)
+                uint32_t lo = 0;
+#pragma unroll
+                for (uint32_t w = H / 2; w > 0; w >>= 1)
+                    if (!kbefore(ku, u, ek[b + lo + w - 1], es[b + lo + w - 1])) lo += w;
+                if (lo < H && !kbefore(ku, u, ek[b + lo], es[b + lo])) lo++;
+                if (lo > 0) r = ev[b + lo - 1];
+                global = lo == H;
+            }
+            if (global) {
+                uint32_t steps = 0;
+                r = representative_cached(W, f, r, u, fb[k], steps);
+                if (steps > kChaseLimit) {
+                    ok = false;
+                    continue;
+                }
+            }
+            if (r != t) st_tri(W + u, tri_pack(u, r));
+        }
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
 }
@@ -710,6 +930,19 @@ static cudaError_t tile_attrs()
 }
 
 template <int V, class Loc>
+static cudaError_t repair_attrs()
+{
+    using VV = Variant<V>;
+    static bool done = false;  // per instantiation
+    if (done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_repair<VV::LX, VV::LY, VV::LZ, 512, Loc>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)RepairShape<VV::LX, VV::LY, VV::LZ>::kSmem);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <int V, class Loc>
 static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, int persistent_grid, bool full,
                              uint32_t *status, cudaStream_t st)
 {
@@ -737,7 +970,9 @@ static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, i
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     PhaseScope ps(kRepair, st);
-    k_repair<VV::LX, VV::LY, VV::LZ, 512, Loc><<<ntiles, 512, 0, st>>>(loc, status);
+    using RS = RepairShape<VV::LX, VV::LY, VV::LZ>;
+    if ((e = repair_attrs<V, Loc>()) != cudaSuccess) return e;
+    k_repair<VV::LX, VV::LY, VV::LZ, 512, Loc><<<ntiles, 512, RS::kSmem, st>>>(loc, status);
     count_launch();
     return cudaGetLastError();
 }
