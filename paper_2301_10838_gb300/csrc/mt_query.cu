@@ -184,56 +184,133 @@ cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint6
 // representative at level t (Algorithm 4 with the value test f(s) <= t that
 // the paper's Representative uses), the deepest vertex of u's component, or
 // 0xFFFFFFFF when f[u] > t. An inner vertex u with f[u] <= t hops to its
-// deepest vertex v first (its link's saddle is u itself), then the chain of
-// branch links is followed while their saddles lie in G_t. The vertices are
-// visited brick by brick (32 x 16 x 16, one CTA each) so that the many
-// vertices sharing a representative find its chain in L1.
+// deepest vertex v first (its link's saddle is u itself); the chain of branch
+// links is then followed while their saddles lie in G_t.
+//
+// One CTA per brick of 32 x 16 x 16 vertices, in three steps: every vertex in
+// G_t enters the start of its chain (its target v, or u itself for a minimum
+// or a root) in a shared-memory hash and keeps the slot; the chain of every
+// hashed start is followed once; every vertex then takes its label from its
+// slot. The vertices of a brick share a few hundred starts, so each vertex
+// costs one read of f and W and one write, and the chases run once per start.
+// A vertex whose start finds no room in the hash follows its chain itself.
 constexpr uint32_t kLabLX = 5, kLabLY = 4, kLabLZ = 4;
+constexpr uint32_t kLabThreads = 512;
+constexpr uint32_t kLabHashLog = 12;  // 4096 slots
+constexpr size_t kLabSmem = ((size_t)8 << kLabHashLog) + ((size_t)2 << (kLabLX + kLabLY + kLabLZ));
 
-__global__ void __launch_bounds__(512) k_labels(const Field f, const uint64_t *__restrict__ W, uint32_t nx,
-                                                uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty, float t,
-                                                uint32_t *__restrict__ labels, uint32_t *status)
+__global__ void __launch_bounds__(kLabThreads, 4) k_labels(const Field f, const uint64_t *__restrict__ W, uint32_t nx,
+                                                           uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty,
+                                                           float t, uint32_t *__restrict__ labels, uint32_t *status)
 {
     const uint32_t n = nx * ny * nz;
     const uint32_t limit = n < kChaseLimit ? n : kChaseLimit;
-    bool bad = false;
     if (*status) return;
     constexpr uint32_t TX = 1u << kLabLX, TY = 1u << kLabLY, TZ = 1u << kLabLZ, TV = TX * TY * TZ;
+    constexpr uint32_t HS = 1u << kLabHashLog, NT = kLabThreads, NB = 4;
+    constexpr uint32_t EMPTY = 0xFFFFFFFFu, kProbes = 16;
+    constexpr uint16_t OUT = 0xFFFFu, SELF = 0xFFFEu;  // slot codes: not in G_t; no room in the hash
+    static_assert(HS <= SELF && TV % (NT * NB) == 0, "slot codes and batches");
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *hkey = smem;               // chain starts
+    uint32_t *hval = hkey + HS;          // their representatives at t
+    uint16_t *vslot = reinterpret_cast<uint16_t *>(hval + HS);  // per vertex: slot or code
+    const unsigned long long *Wq = reinterpret_cast<const unsigned long long *>(W);
+
     const uint32_t tile = blockIdx.x;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
     const uint32_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
     const uint32_t wx = min(TX, nx - x0), wy = min(TY, ny - y0), wz = min(TZ, nz - z0);
     const uint32_t nxy = nx * ny;
     const uint32_t base = z0 * nxy + y0 * nx + x0;
-    bool ok = true;
-    for (uint32_t l = threadIdx.x; l < TV; l += blockDim.x) {
-        const uint32_t lx = l & (TX - 1), ly = (l >> kLabLX) & (TY - 1), lz = l >> (kLabLX + kLabLY);
-        if (lx >= wx || ly >= wy || lz >= wz) continue;
-        const uint32_t u = base + lz * nxy + ly * nx + lx;
-        uint32_t lab = 0xFFFFFFFFu;
-        if (f[u] <= t) {
-            // the caller's triplets are followed only through ids < n, and
-            // for at most `limit` links: a chain of a valid tree is shorter
-            // than n, so a longer one means a cycle
-            uint32_t x = u;
-            for (uint32_t h = 0;; h++) {
-                const uint64_t T = __ldg(reinterpret_cast<const unsigned long long *>(W) + x);
-                const uint32_t s = tri_s(T);
-                if (T == tri_pack(x, x)) break;
-                if (s >= n || tri_v(T) >= n) {
-                    bad = true;
-                    break;
-                }
-                if (!(f[s] <= t)) break;
-                x = tri_v(T);
-                if (h >= limit) {
-                    ok = false;
-                    break;
-                }
+    auto gid_of = [&](uint32_t l) {
+        return base + (l >> (kLabLX + kLabLY)) * nxy + ((l >> kLabLX) & (TY - 1)) * nx + (l & (TX - 1));
+    };
+    auto inside = [&](uint32_t l) {
+        return (l & (TX - 1)) < wx && ((l >> kLabLX) & (TY - 1)) < wy && (l >> (kLabLX + kLabLY)) < wz;
+    };
+    // representative at t of the chain from x: the caller's triplets are
+    // followed only through ids < n, and for at most `limit` links (a chain
+    // of a valid tree is shorter than n, so a longer one means a cycle)
+    bool ok = true, bad = false;
+    auto chase = [&](uint32_t x) -> uint32_t {
+        for (uint32_t h = 0;; h++) {
+            const uint64_t T = __ldg(Wq + x);
+            const uint32_t s = tri_s(T);
+            if (T == tri_pack(x, x)) return x;
+            if (s >= n || tri_v(T) >= n) {
+                bad = true;
+                return x;
             }
-            lab = x;
+            if (!(f[s] <= t)) return x;
+            x = tri_v(T);
+            if (h >= limit) {
+                ok = false;
+                return x;
+            }
         }
-        labels[u] = lab;
+    };
+
+    for (uint32_t i = threadIdx.x; i < HS; i += NT) hkey[i] = EMPTY;
+    __syncthreads();
+
+    // 1. chain starts into the hash
+    volatile uint32_t *vhk = hkey;
+    for (uint32_t l0 = 0; l0 < TV; l0 += NT * NB) {
+        uint64_t Tb[NB];
+        float fb[NB];
+#pragma unroll
+        for (uint32_t k = 0; k < NB; k++) {
+            const uint32_t l = l0 + k * NT + threadIdx.x;
+            const uint32_t u = gid_of(l);
+            const bool in = inside(l);
+            fb[k] = in ? f[u] : 0.0f;
+            Tb[k] = in ? __ldg(Wq + u) : tri_pack(u, u);
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < NB; k++) {
+            const uint32_t l = l0 + k * NT + threadIdx.x;
+            if (!inside(l)) continue;
+            const uint32_t u = gid_of(l);
+            if (!(fb[k] <= t)) {
+                vslot[l] = OUT;
+                continue;
+            }
+            const uint32_t s = tri_s(Tb[k]), v = tri_v(Tb[k]);
+            if (s >= n || v >= n) {  // leave it to the vertex's own chase, which reports it
+                vslot[l] = SELF;
+                continue;
+            }
+            const uint32_t st = (s == u && v != u) ? v : u;
+            uint32_t h = (st * 0x9E3779B1u) >> (32 - kLabHashLog);
+            uint16_t slot = SELF;
+            for (uint32_t p = 0; p < kProbes; p++) {
+                uint32_t kk = vhk[h];
+                if (kk == EMPTY) kk = atomicCAS(hkey + h, EMPTY, st);
+                if (kk == EMPTY || kk == st) {
+                    slot = (uint16_t)h;
+                    break;
+                }
+                h = (h + 1) & (HS - 1);
+            }
+            vslot[l] = slot;
+        }
+    }
+    __syncthreads();
+
+    // 2. one chase per hashed start
+    for (uint32_t i = threadIdx.x; i < HS; i += NT) {
+        const uint32_t st = hkey[i];
+        if (st != EMPTY) hval[i] = chase(st);
+    }
+    __syncthreads();
+
+    // 3. labels
+    for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+        if (!inside(l)) continue;
+        const uint32_t u = gid_of(l);
+        const uint16_t c = vslot[l];
+        labels[u] = c == OUT ? 0xFFFFFFFFu : c == SELF ? chase(u) : hval[c];
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
     if (bad) raise_status(status, ST_CORRUPT);
@@ -245,7 +322,15 @@ cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32
     PhaseScope ps(kLabels, st);
     count_launch();
     const uint32_t ntx = (nx + 31) >> kLabLX, nty = (ny + 15) >> kLabLY, ntz = (nz + 15) >> kLabLZ;
-    k_labels<<<ntx * nty * ntz, 512, 0, st>>>(Field{f, sg}, W, nx, ny, nz, ntx, nty, t, labels, ws.status);
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLabSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_labels<<<ntx * nty * ntz, kLabThreads, kLabSmem, st>>>(Field{f, sg}, W, nx, ny, nz, ntx, nty, t, labels,
+                                                            ws.status);
     return cudaGetLastError();
 }
 
