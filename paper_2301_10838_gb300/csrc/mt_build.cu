@@ -100,20 +100,50 @@ __device__ __forceinline__ bool kbefore(uint32_t ka, uint32_t a, uint32_t kb, ui
 // Climb (Algorithm 3 / 4) in the tile's tree from x through links whose
 // saddle is at or below (kS, S); a root stops it. Chains lead to ever earlier
 // vertices, so a walk longer than the tile means a corrupted tree (ok=false).
+// The next vertex's triplet is read together with the saddle's key, before
+// the test that decides whether it is needed (indices are masked to the
+// tile, so a read that turns out unneeded stays in bounds).
 template <int TV>
 __device__ __forceinline__ uint32_t sm_climb(const uint32_t *T, const uint32_t *K, uint32_t x, uint32_t S,
                                              uint32_t kS, uint32_t &w, bool &ok)
 {
     const volatile uint32_t *vT = T;
+    uint32_t wx = vT[x];
     for (uint32_t h = 0; h < (uint32_t)TV; h++) {
-        w = vT[x];
-        if (w == sm_pack(x, x)) return x;
-        const uint32_t s = sm_s(w);
-        if (s != S && !kbefore(K[s], s, kS, S)) return x;
-        x = sm_v(w);
+        const uint32_t s = sm_s(wx), nx = sm_v(wx);
+        const uint32_t ks = K[s & (TV - 1)];
+        const uint32_t wn = vT[nx & (TV - 1)];
+        if (wx == sm_pack(x, x) || (s != S && !kbefore(ks, s, kS, S))) {
+            w = wx;
+            return x;
+        }
+        x = nx;
+        wx = wn;
     }
     ok = false;
+    w = wx;
     return x;
+}
+
+// Both climbs of a merge side by side, so that their reads overlap.
+template <int TV>
+__device__ __forceinline__ void sm_climb2(const uint32_t *T, const uint32_t *K, uint32_t &u, uint32_t &v,
+                                          uint32_t S, uint32_t kS, uint32_t &wu, uint32_t &wv, bool &ok)
+{
+    const volatile uint32_t *vT = T;
+    wu = vT[u], wv = vT[v];
+    bool du = false, dv = false;
+    for (uint32_t h = 0; h < 2u * TV; h++) {
+        const uint32_t su = sm_s(wu), nu = sm_v(wu), sv = sm_s(wv), nv = sm_v(wv);
+        const uint32_t ku = K[su & (TV - 1)], kv = K[sv & (TV - 1)];
+        const uint32_t wnu = vT[nu & (TV - 1)], wnv = vT[nv & (TV - 1)];
+        du = du || wu == sm_pack(u, u) || (su != S && !kbefore(ku, su, kS, S));
+        dv = dv || wv == sm_pack(v, v) || (sv != S && !kbefore(kv, sv, kS, S));
+        if (du && dv) return;
+        if (!du) u = nu, wu = wnu;
+        if (!dv) v = nv, wv = wnv;
+    }
+    ok = false;
 }
 
 // Merge (Algorithm 3) on the tile's shared-memory tree, lock-free with 32-bit
@@ -127,8 +157,7 @@ __device__ __forceinline__ void sm_merge(uint32_t *T, const uint32_t *K, uint32_
     uint32_t u = a, v = c;
     for (uint32_t it = 0; it < kMergeStepLimit; it++) {
         uint32_t Tu, Tv;
-        u = sm_climb<TV>(T, K, u, S, kS, Tu, ok);
-        v = sm_climb<TV>(T, K, v, S, kS, Tv, ok);
+        sm_climb2<TV>(T, K, u, v, S, kS, Tu, Tv, ok);
         if (!ok || u == v) return;
         if (kbefore(K[v], v, K[u], u)) {
             const uint32_t x = u;
