@@ -132,6 +132,34 @@ mt_status mt_components_at_ex(const float *d_f, const uint64_t *d_W, mt_grid g, 
                               uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
+ * Persistence simplification (Section 1: the diagram measures the importance
+ * of branches, and short branches are noise). A branch -- minimum u, saddle s
+ * with W[u].s == s != u -- has persistence p = f(s) - f(u), computed in
+ * float32 on the values the order uses (-f with MT_SUPERLEVEL). Simplifying by
+ * eps fills every branch of persistence below eps up to its saddle, which
+ * removes exactly those pairs from the diagram and leaves all others.
+ *
+ * mt_simplified_pairs: the pairs (u, s) with p >= eps, by ascending u, with
+ * the arguments, synchronisation and return codes of mt_persistence_pairs
+ * (eps <= 0 gives all pairs). flags must be those of the build (0 or
+ * MT_SUPERLEVEL). eps must not be NaN.
+ *
+ * mt_simplified_components_at: the components of G_t of the simplified field.
+ * A component of G_t whose representative r heads a branch with p < eps lies
+ * inside a filled pit and leaves G_t: its vertices get 0xFFFFFFFF. Every other
+ * vertex gets the label mt_components_at_ex gives it (the elder rule makes a
+ * branch at least as persistent as any branch that merges into it, so no long
+ * branch lies inside a filled pit). eps <= 0 gives mt_components_at_ex's
+ * labels. Asynchronous; errors as mt_components_at. t and eps must not be NaN.
+ */
+mt_status mt_simplified_pairs(const float *d_f, const uint64_t *d_W, mt_grid g, float eps, uint32_t flags,
+                              uint32_t *d_pairs, uint64_t cap, uint64_t *h_npairs, uint32_t *h_root, void *d_ws,
+                              size_t ws_bytes, void *stream);
+
+mt_status mt_simplified_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, float t, float eps,
+                                      uint32_t flags, uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
  * Synchronise `stream` and return (then clear) the workspace status word:
  * MT_OK, MT_ERR_NONFINITE, MT_ERR_TIMEOUT or MT_ERR_CAPACITY.
  */

@@ -13,6 +13,9 @@ Functions
   pairs(W)                 -> (pairs uint32[k, 2] = (minimum, saddle), roots)
   components(f, t)         -> labels (uint32[n]; 0xFFFFFFFF outside G_t)
   point_triplet(f, u, budget) -> W[u] or None if the query exceeds budget
+  simplified_pairs(f, W, eps) -> the pairs of persistence >= eps
+  simplified_components(f, W, t, eps) -> labels of G_t after filling every
+                           branch of persistence < eps up to its saddle
 """
 
 from __future__ import annotations
@@ -154,3 +157,43 @@ def point_triplet(f, u: int, budget: int = 1 << 20):
     if r < 0:
         raise OracleError(r)
     return int(out.value) if r == 1 else None
+
+
+def persistence(f, W: np.ndarray, u) -> np.ndarray:
+    """float32 persistence f(s) - f(u) of the branches born at the minima u
+    (s = W[u].s; the subtraction is done in float32, as the GPU path does)."""
+    g = np.ascontiguousarray(np.asarray(f, dtype=np.float32)).ravel()
+    u = np.asarray(u, dtype=np.int64)
+    s = (np.asarray(W, dtype=np.uint64).ravel()[u] >> np.uint64(32)).astype(np.int64)
+    return g[s] - g[u]
+
+
+def simplified_pairs(f, W: np.ndarray, eps: float) -> np.ndarray:
+    """Persistence simplification of the diagram (Section 1: a branch's
+    persistence measures its importance; short ones are noise): the pairs
+    (minimum u, saddle s) with float32 f(s) - f(u) >= eps, by ascending u."""
+    p, _ = pairs(W)
+    if len(p) == 0:
+        return p
+    keep = persistence(f, W, p[:, 0]) >= np.float32(eps)
+    return p[keep]
+
+
+def simplified_components(f, W: np.ndarray, t: float, eps: float) -> np.ndarray:
+    """Components of G_t after filling every branch of persistence < eps up to
+    its saddle. The components of G_t come from ``components`` (union-find
+    over the mask, no tree); a component whose deepest vertex r heads a branch
+    of W (r not a root) with float32 persistence < eps lies inside a filled
+    pit and leaves G_t (label 0xFFFFFFFF); every other component keeps its
+    label."""
+    lab = components(f, t)
+    inside = lab != np.uint32(0xFFFFFFFF)
+    reps = np.unique(lab[inside]).astype(np.int64)
+    if len(reps) == 0:
+        return lab
+    Wf = np.asarray(W, dtype=np.uint64).ravel()
+    s = (Wf[reps] >> np.uint64(32)).astype(np.int64)
+    short = (s != reps) & (persistence(f, Wf, reps) < np.float32(eps))
+    out = lab.copy()
+    out[np.isin(lab, reps[short].astype(np.uint32)) & inside] = np.uint32(0xFFFFFFFF)
+    return out

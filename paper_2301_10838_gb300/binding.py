@@ -37,6 +37,8 @@ __all__ = [
     "mt_build_triplets_ex",
     "mt_components_at_ex",
     "mt_persistence_pairs_noalloc",
+    "mt_simplified_pairs",
+    "mt_simplified_components_at",
     "BatchPlan",
     "mt_batch_workspace_bytes",
     "mt_batch_prepare",
@@ -99,6 +101,10 @@ _SIGS = {
     "mt_components_at_ex": ([_P, _P, Grid, ctypes.c_float, ctypes.c_uint32, _P, _P, ctypes.c_size_t, _P],
                             ctypes.c_int32),
     "mt_persistence_pairs_noalloc": ([_P, _P, Grid, _P, _U64, _P, _P, _P], ctypes.c_int32),
+    "mt_simplified_pairs": ([_P, _P, Grid, ctypes.c_float, ctypes.c_uint32, _P, _U64, _P, _P, _P, ctypes.c_size_t, _P],
+                            ctypes.c_int32),
+    "mt_simplified_components_at": ([_P, _P, Grid, ctypes.c_float, ctypes.c_float, ctypes.c_uint32, _P, _P,
+                                     ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_batch_workspace_bytes": ([_P, ctypes.c_uint32], ctypes.c_size_t),
     "mt_batch_prepare": ([_P, _P, ctypes.c_uint32, _P, _P, _P, ctypes.c_size_t, _P, _P], ctypes.c_int32),
     "mt_batch_launch": ([_P, ctypes.c_int, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
@@ -242,6 +248,42 @@ def mt_persistence_pairs(f: torch.Tensor, W: torch.Tensor, pairs: torch.Tensor, 
         return int(npairs.value), int(root.value)
     _check(code, "mt_persistence_pairs", f" npairs={npairs.value} cap={cap}")
     return int(npairs.value), int(root.value)
+
+
+def mt_simplified_pairs(f: torch.Tensor, W: torch.Tensor, eps: float, flags: int, pairs: torch.Tensor,
+                        ws: torch.Tensor, stream=None, allow_partial: bool = False) -> tuple[int, int]:
+    """The pairs of persistence >= eps (float32 f(s) - f(u), on -f with
+    MT_SUPERLEVEL) as (minimum, saddle) rows of ``pairs``; returns
+    (npairs, root). Synchronises the stream."""
+    g = grid_of(f)
+    n = f.numel()
+    pf = _dev(f, "f", (torch.float32,))
+    pW = _dev(W, "W", _I64, n)
+    pws = _dev(ws, "ws", (torch.uint8,))
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must have shape (cap, 2)")
+    cap = int(pairs.shape[0])
+    pp = _dev(pairs, "pairs", _I32) if cap else 0
+    npairs = ctypes.c_uint64(0)
+    root = ctypes.c_uint32(0xFFFFFFFF)
+    code = load().mt_simplified_pairs(pf, pW, g, float(eps), int(flags), pp, cap, ctypes.byref(npairs),
+                                      ctypes.byref(root), pws, ws.numel(), _stream_ptr(stream))
+    if code == -4 and allow_partial:
+        return int(npairs.value), int(root.value)
+    _check(code, "mt_simplified_pairs", f" npairs={npairs.value} cap={cap}")
+    return int(npairs.value), int(root.value)
+
+
+def mt_simplified_components_at(f: torch.Tensor, W: torch.Tensor, t: float, eps: float, flags: int,
+                                labels: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    """Labels of G_t after filling every branch of persistence < eps up to its
+    saddle (0xFFFFFFFF outside the simplified G_t)."""
+    g = grid_of(f)
+    n = f.numel()
+    _check(load().mt_simplified_components_at(_dev(f, "f", (torch.float32,)), _dev(W, "W", _I64, n), g, float(t),
+                                              float(eps), int(flags), _dev(labels, "labels", _I32, n),
+                                              _dev(ws, "ws", (torch.uint8,)), ws.numel(), _stream_ptr(stream)),
+           "mt_simplified_components_at")
 
 
 def mt_persistence_pairs_noalloc(f: torch.Tensor, W: torch.Tensor, pairs: torch.Tensor, stream=None,

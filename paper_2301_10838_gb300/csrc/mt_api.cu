@@ -151,6 +151,52 @@ mt_status mt_persistence_pairs(const float *d_f, const uint64_t *d_W, mt_grid g,
     return meta[0] > cap ? MT_ERR_CAPACITY : MT_OK;
 }
 
+mt_status mt_simplified_pairs(const float *d_f, const uint64_t *d_W, mt_grid g, float eps, uint32_t flags,
+                              uint32_t *d_pairs, uint64_t cap, uint64_t *h_npairs, uint32_t *h_root, void *d_ws,
+                              size_t ws_bytes, void *stream)
+{
+    uint64_t n;
+    mt_status st = grid_n(g, n);
+    if (st != MT_OK) return st;
+    if (!d_f || !d_W || !h_npairs || std::isnan(eps) || ((uintptr_t)d_f & 3) || ((uintptr_t)d_W & 7) ||
+        (cap && (!d_pairs || ((uintptr_t)d_pairs & 3))) || (flags & ~MT_SUPERLEVEL))
+        return MT_ERR_INVALID;
+    Workspace ws;
+    if (!carve_workspace(d_ws, ws_bytes, n, ws)) return MT_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float sg = (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f;
+    if (launch_pairs(d_W, n, d_pairs, cap, ws, s, d_f, sg, eps) != cudaSuccess) return MT_ERR_CUDA;
+    uint64_t meta[3] = {0, 0, 0};
+    uint32_t bits = 0;
+    if (cudaMemcpyAsync(meta, ws.meta, sizeof(meta), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MT_ERR_CUDA;
+    if (cudaMemcpyAsync(&bits, ws.status, sizeof(bits), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return MT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MT_ERR_CUDA;
+    if (bits) return status_from_bits(bits);
+    *h_npairs = meta[0];
+    if (h_root) *h_root = meta[1] == 1 ? (uint32_t)meta[2] : 0xFFFFFFFFu;
+    if (meta[1] != 1) return MT_ERR_INVALID;  // not a tree of a connected grid
+    return meta[0] > cap ? MT_ERR_CAPACITY : MT_OK;
+}
+
+mt_status mt_simplified_components_at(const float *d_f, const uint64_t *d_W, mt_grid g, float t, float eps,
+                                      uint32_t flags, uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream)
+{
+    uint64_t n;
+    mt_status st = grid_n(g, n);
+    if (st != MT_OK) return st;
+    if (!d_f || !d_W || !d_labels || std::isnan(t) || std::isnan(eps) || ((uintptr_t)d_f & 3) ||
+        ((uintptr_t)d_W & 7) || ((uintptr_t)d_labels & 3) || (flags & ~MT_SUPERLEVEL))
+        return MT_ERR_INVALID;
+    Workspace ws;
+    if (!carve_workspace(d_ws, ws_bytes, n, ws)) return MT_ERR_INVALID;
+    const float sg = (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f;
+    if (launch_labels(d_f, d_W, g.nx, g.ny, g.nz, sg * t, sg, d_labels, ws, static_cast<cudaStream_t>(stream), eps) !=
+        cudaSuccess)
+        return MT_ERR_CUDA;
+    return MT_OK;
+}
+
 mt_status mt_components_at_ex(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t flags,
                               uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream)
 {

@@ -68,8 +68,10 @@ int device_sms();
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
                          uint32_t *faces, float sg, cudaStream_t st);
+// f, sg, eps: persistence simplification (pairs of persistence below eps
+// dropped; eps <= 0 keeps all and does not read f)
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
-                         cudaStream_t st);
+                         cudaStream_t st, const float *f = nullptr, float sg = 1.0f, float eps = 0.0f);
 
 // Batched build and pairs over a packed descriptor table already in device
 // memory; variant selects the tile shape (mt_build.cu, mt_query.cu).
@@ -79,6 +81,6 @@ cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint6
                                uint64_t *npairs, const uint32_t *status, cudaStream_t st);
 void tile_shape(int variant, uint32_t &tx, uint32_t &ty, uint32_t &tz);
 cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, float t,
-                          float sg, uint32_t *labels, Workspace &ws, cudaStream_t st);
+                          float sg, uint32_t *labels, Workspace &ws, cudaStream_t st, float eps = 0.0f);
 
 }  // namespace mt

@@ -22,12 +22,25 @@ namespace mt {
 // 16 triplets in registers, ranks its flags with ballots, and one barrier
 // combines the 8 warp totals, which keeps the ascending order.
 constexpr int kCompactThreads = 256;
+
+// Persistence simplification: the pair (u, s) of a branch minimum u is kept
+// when its persistence f(s) - f(u), computed in float32 on the values the
+// order sees (sg * f), is at least eps. eps <= 0 keeps every pair without
+// reading f (a persistence is never negative).
+__device__ __forceinline__ bool keep_pair(const FieldDesc &fd, uint64_t T, uint32_t u, float eps)
+{
+    if (tri_s(T) == u) return false;
+    if (!(eps > 0.0f)) return true;
+    const float fu = fd.sg * __ldg(fd.f + u), fs = fd.sg * __ldg(fd.f + tri_s(T));
+    return fs - fu >= eps;
+}
 constexpr int kCompactWarps = kCompactThreads / 32;
 constexpr int kCompactRows = kCompactChunk / kCompactThreads;  // rows of 32 per warp
 static_assert(kCompactRows * 32 * kCompactWarps == kCompactChunk, "chunk = warps x rows x 32");
 
 template <class Loc>
-__global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32_t *counts, const uint32_t *status)
+__global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32_t *counts, float eps,
+                                                                 const uint32_t *status)
 {
     if (*status) return;
     __shared__ uint32_t warp_sum[kCompactWarps];
@@ -45,7 +58,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32
         if (u >= n) break;
         const uint64_t T = W[u];
         if (tri_s(T) != (uint32_t)u) {
-            c++;
+            c += keep_pair(fd, T, (uint32_t)u, eps);
         } else if (tri_v(T) == (uint32_t)u) {
             atomicAdd(reinterpret_cast<unsigned long long *>(fd.meta + 1), 1ull);
             fd.meta[2] = u;
@@ -99,7 +112,7 @@ __global__ void __launch_bounds__(1024) k_scan_counts(Loc loc, uint32_t *counts,
 }
 
 template <class Loc>
-__global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const uint32_t *offsets,
+__global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const uint32_t *offsets, float eps,
                                                                  const uint32_t *status)
 {
     if (*status) return;
@@ -118,7 +131,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const 
     for (int r = 0; r < kCompactRows; r++) {
         const uint64_t u = b0 + (uint64_t)r * 32 + lane;
         Tr[r] = u < n ? W[u] : tri_pack((uint32_t)u, (uint32_t)u);  // past the end: no pair
-        c += __popc(__ballot_sync(0xffffffffu, tri_s(Tr[r]) != (uint32_t)u));
+        c += __popc(__ballot_sync(0xffffffffu, keep_pair(fd, Tr[r], (uint32_t)u, eps)));
     }
     if (lane == 0) warp_cnt[warp] = c;
     __syncthreads();
@@ -128,7 +141,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const 
 #pragma unroll
     for (int r = 0; r < kCompactRows; r++) {
         const uint64_t u = b0 + (uint64_t)r * 32 + lane;
-        const bool flag = tri_s(Tr[r]) != (uint32_t)u;
+        const bool flag = keep_pair(fd, Tr[r], (uint32_t)u, eps);
         const uint32_t ball = __ballot_sync(0xffffffffu, flag);
         if (flag) {
             const uint64_t pos = run + __popc(ball & below);
@@ -143,21 +156,21 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const 
 
 template <class Loc>
 static cudaError_t run_pairs(const Loc &loc, uint32_t nfields, uint64_t nchunks, uint32_t *counts, uint64_t *npairs,
-                             const uint32_t *status, cudaStream_t st)
+                             const uint32_t *status, cudaStream_t st, float eps = 0.0f)
 {
     PhaseScope ps(kPairs, st);
     count_launch(3);
-    k_pairs_count<Loc><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, status);
+    k_pairs_count<Loc><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, eps, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_scan_counts<Loc><<<nfields, 1024, 0, st>>>(loc, counts, npairs, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_pairs_write<Loc><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, status);
+    k_pairs_write<Loc><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, eps, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
-                         cudaStream_t st)
+                         cudaStream_t st, const float *f, float sg, float eps)
 {
     cudaError_t e = cudaMemsetAsync(ws.meta, 0, 3 * sizeof(uint64_t), st);
     if (e != cudaSuccess) return e;
@@ -168,7 +181,9 @@ cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_
     loc.d.meta = ws.meta;
     loc.d.n = n;
     loc.d.cap = cap;
-    return run_pairs(loc, 1, ws.nchunks, ws.counts, nullptr, ws.status, st);
+    loc.d.f = f;
+    loc.d.sg = sg;
+    return run_pairs(loc, 1, ws.nchunks, ws.counts, nullptr, ws.status, st, eps);
 }
 
 cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint64_t nchunks, uint32_t *counts,
@@ -194,6 +209,14 @@ cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint6
 // slot. The vertices of a brick share a few hundred starts, so each vertex
 // costs one read of f and W and one write, and the chases run once per start.
 // A vertex whose start finds no room in the hash follows its chain itself.
+//
+// With eps > 0 the labels are those of the simplified field in which every
+// branch of persistence below eps is filled up to its saddle: a component of
+// G_t whose representative r heads such a branch (r not the root, f(s) - f(r)
+// < eps in float32 for r's saddle s) lies inside a filled pit and leaves G_t,
+// its vertices labelled 0xFFFFFFFF. No other component changes: by the elder
+// rule a branch is never less persistent than one that merges into it, so a
+// long branch never lies inside a short one's pit.
 constexpr uint32_t kLabLX = 5, kLabLY = 4, kLabLZ = 4;
 constexpr uint32_t kLabThreads = 512;
 constexpr uint32_t kLabHashLog = 12;  // 4096 slots
@@ -201,7 +224,8 @@ constexpr size_t kLabSmem = ((size_t)8 << kLabHashLog) + ((size_t)2 << (kLabLX +
 
 __global__ void __launch_bounds__(kLabThreads, 4) k_labels(const Field f, const uint64_t *__restrict__ W, uint32_t nx,
                                                            uint32_t ny, uint32_t nz, uint32_t ntx, uint32_t nty,
-                                                           float t, uint32_t *__restrict__ labels, uint32_t *status)
+                                                           float t, float eps, uint32_t *__restrict__ labels,
+                                                           uint32_t *status)
 {
     const uint32_t n = nx * ny * nz;
     const uint32_t limit = n < kChaseLimit ? n : kChaseLimit;
@@ -249,6 +273,14 @@ __global__ void __launch_bounds__(kLabThreads, 4) k_labels(const Field f, const 
                 return x;
             }
         }
+    };
+    // the representative, or 0xFFFFFFFF if it heads a branch shorter than eps
+    auto simplified = [&](uint32_t r) -> uint32_t {
+        if (!(eps > 0.0f)) return r;
+        const uint64_t T = __ldg(Wq + r);
+        const uint32_t s = tri_s(T);
+        if (s == r || s >= n) return r;  // the root (or an inner vertex of a corrupt tree)
+        return f[s] - f[r] >= eps ? r : 0xFFFFFFFFu;
     };
 
     for (uint32_t i = threadIdx.x; i < HS; i += NT) hkey[i] = EMPTY;
@@ -301,7 +333,7 @@ __global__ void __launch_bounds__(kLabThreads, 4) k_labels(const Field f, const 
     // 2. one chase per hashed start
     for (uint32_t i = threadIdx.x; i < HS; i += NT) {
         const uint32_t st = hkey[i];
-        if (st != EMPTY) hval[i] = chase(st);
+        if (st != EMPTY) hval[i] = simplified(chase(st));
     }
     __syncthreads();
 
@@ -310,14 +342,14 @@ __global__ void __launch_bounds__(kLabThreads, 4) k_labels(const Field f, const 
         if (!inside(l)) continue;
         const uint32_t u = gid_of(l);
         const uint16_t c = vslot[l];
-        labels[u] = c == OUT ? 0xFFFFFFFFu : c == SELF ? chase(u) : hval[c];
+        labels[u] = c == OUT ? 0xFFFFFFFFu : c == SELF ? simplified(chase(u)) : hval[c];
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
     if (bad) raise_status(status, ST_CORRUPT);
 }
 
 cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, float t,
-                          float sg, uint32_t *labels, Workspace &ws, cudaStream_t st)
+                          float sg, uint32_t *labels, Workspace &ws, cudaStream_t st, float eps)
 {
     PhaseScope ps(kLabels, st);
     count_launch();
@@ -329,8 +361,8 @@ cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_labels<<<ntx * nty * ntz, kLabThreads, kLabSmem, st>>>(Field{f, sg}, W, nx, ny, nz, ntx, nty, t, labels,
-                                                            ws.status);
+    k_labels<<<ntx * nty * ntz, kLabThreads, kLabSmem, st>>>(Field{f, sg}, W, nx, ny, nz, ntx, nty, t, eps,
+                                                            labels, ws.status);
     return cudaGetLastError();
 }
 
