@@ -62,28 +62,34 @@ struct Field {
     __device__ __forceinline__ float operator[](uint32_t i) const { return sg * __ldg(f + i); }
 };
 
-// Follow the triplet links from x while the link's saddle is at or below
-// level S (vertex order), i.e. walk to the deepest vertex that the current
-// tree connects to x below S (the climbs of Algorithm 3). Returns the word
-// of the vertex where it stops and leaves that vertex in x. A root word
-// (x, x) always stops the walk (the paper's pseudocode has no guard for it).
-// The next vertex's word is loaded together with the saddle's value, before
-// the level test, so that a hop costs one memory latency instead of two.
-__device__ __forceinline__ uint64_t climb(const uint64_t *W, const Field f, uint32_t &x, uint32_t S, float fS,
-                                          uint32_t &steps)
+// Climbs (Algorithm 3): follow the triplet links from a vertex while the
+// link's saddle is at or below level S (vertex order), i.e. walk to the
+// deepest vertex that the current tree connects to it below S. A root word
+// (x, x) always stops a walk (the paper's pseudocode has no guard for it).
+// Both climbs of a merge side by side, so that their loads overlap: each
+// round reads, for every walk still going, its saddle's value and (before the
+// level test) its next vertex's word.
+__device__ __forceinline__ void climb2(const uint64_t *W, const Field f, uint32_t &u, uint32_t &v, uint32_t S,
+                                       float fS, uint64_t &Tu, uint64_t &Tv, uint32_t &steps)
 {
-    uint64_t T = ld_tri(W + x);
+    Tu = ld_tri(W + u);
+    Tv = ld_tri(W + v);
+    bool du = false, dv = false;
     for (;;) {
-        const uint32_t s = tri_s(T), t = tri_v(T);
-        if (s == x && t == x) break;  // root
-        const float fs = f[s];
-        const uint64_t Tn = ld_tri(W + t);
-        if (s != S && !before(fs, s, fS, S)) break;  // saddle above S
-        x = t;
-        T = Tn;
-        if (++steps > kMergeStepLimit) break;
+        const uint32_t su = tri_s(Tu), tu = tri_v(Tu), sv = tri_s(Tv), tv = tri_v(Tv);
+        du = du || (su == u && tu == u);
+        dv = dv || (sv == v && tv == v);
+        float fsu = 0.0f, fsv = 0.0f;
+        uint64_t Tnu = 0, Tnv = 0;
+        if (!du) fsu = f[su], Tnu = ld_tri(W + tu);
+        if (!dv) fsv = f[sv], Tnv = ld_tri(W + tv);
+        du = du || (su != S && !before(fsu, su, fS, S));
+        dv = dv || (sv != S && !before(fsv, sv, fS, S));
+        if (du && dv) return;
+        if (!du) u = tu, Tu = Tnu;
+        if (!dv) v = tv, Tv = Tnv;
+        if (++steps > kMergeStepLimit) return;
     }
-    return T;
 }
 
 // Algorithm 3 (Merge), lock-free: make a and b connected at level S in the
@@ -103,8 +109,8 @@ __device__ __forceinline__ bool merge(uint64_t *W, const Field f, uint32_t S, ui
     uint32_t u = a, v = b;
     uint32_t steps = 0;
     for (;;) {
-        uint64_t Tu = climb(W, f, u, S, fS, steps);
-        uint64_t Tv = climb(W, f, v, S, fS, steps);
+        uint64_t Tu, Tv;
+        climb2(W, f, u, v, S, fS, Tu, Tv, steps);
         if (++steps > kMergeStepLimit) return false;
         if (u == v) return true;
         if (before(f[v], v, f[u], u)) {

@@ -23,14 +23,16 @@ namespace mt {
 // combines the 8 warp totals, which keeps the ascending order.
 constexpr int kCompactThreads = 256;
 
-// Persistence simplification: the pair (u, s) of a branch minimum u is kept
-// when its persistence f(s) - f(u), computed in float32 on the values the
-// order sees (sg * f), is at least eps. eps <= 0 keeps every pair without
-// reading f (a persistence is never negative).
+// Persistence simplification (SIMP): the pair (u, s) of a branch minimum u is
+// kept when its persistence f(s) - f(u), computed in float32 on the values
+// the order sees (sg * f), is at least eps. Without SIMP every pair is kept
+// and f is not read (a separate instantiation, so that the plain kernels
+// keep their loads of all rows ahead of any use).
+template <bool SIMP>
 __device__ __forceinline__ bool keep_pair(const FieldDesc &fd, uint64_t T, uint32_t u, float eps)
 {
     if (tri_s(T) == u) return false;
-    if (!(eps > 0.0f)) return true;
+    if (!SIMP) return true;
     const float fu = fd.sg * __ldg(fd.f + u), fs = fd.sg * __ldg(fd.f + tri_s(T));
     return fs - fu >= eps;
 }
@@ -38,7 +40,7 @@ constexpr int kCompactWarps = kCompactThreads / 32;
 constexpr int kCompactRows = kCompactChunk / kCompactThreads;  // rows of 32 per warp
 static_assert(kCompactRows * 32 * kCompactWarps == kCompactChunk, "chunk = warps x rows x 32");
 
-template <class Loc>
+template <class Loc, bool SIMP>
 __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32_t *counts, float eps,
                                                                  const uint32_t *status)
 {
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32
         if (u >= n) break;
         const uint64_t T = W[u];
         if (tri_s(T) != (uint32_t)u) {
-            c += keep_pair(fd, T, (uint32_t)u, eps);
+            c += keep_pair<SIMP>(fd, T, (uint32_t)u, eps);
         } else if (tri_v(T) == (uint32_t)u) {
             atomicAdd(reinterpret_cast<unsigned long long *>(fd.meta + 1), 1ull);
             fd.meta[2] = u;
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(1024) k_scan_counts(Loc loc, uint32_t *counts,
     }
 }
 
-template <class Loc>
+template <class Loc, bool SIMP>
 __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const uint32_t *offsets, float eps,
                                                                  const uint32_t *status)
 {
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const 
     for (int r = 0; r < kCompactRows; r++) {
         const uint64_t u = b0 + (uint64_t)r * 32 + lane;
         Tr[r] = u < n ? W[u] : tri_pack((uint32_t)u, (uint32_t)u);  // past the end: no pair
-        c += __popc(__ballot_sync(0xffffffffu, keep_pair(fd, Tr[r], (uint32_t)u, eps)));
+        c += __popc(__ballot_sync(0xffffffffu, keep_pair<SIMP>(fd, Tr[r], (uint32_t)u, eps)));
     }
     if (lane == 0) warp_cnt[warp] = c;
     __syncthreads();
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const 
 #pragma unroll
     for (int r = 0; r < kCompactRows; r++) {
         const uint64_t u = b0 + (uint64_t)r * 32 + lane;
-        const bool flag = keep_pair(fd, Tr[r], (uint32_t)u, eps);
+        const bool flag = keep_pair<SIMP>(fd, Tr[r], (uint32_t)u, eps);
         const uint32_t ball = __ballot_sync(0xffffffffu, flag);
         if (flag) {
             const uint64_t pos = run + __popc(ball & below);
@@ -160,12 +162,15 @@ static cudaError_t run_pairs(const Loc &loc, uint32_t nfields, uint64_t nchunks,
 {
     PhaseScope ps(kPairs, st);
     count_launch(3);
-    k_pairs_count<Loc><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, eps, status);
+    const bool simp = eps > 0.0f;
+    if (simp) k_pairs_count<Loc, true><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, eps, status);
+    else k_pairs_count<Loc, false><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, eps, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_scan_counts<Loc><<<nfields, 1024, 0, st>>>(loc, counts, npairs, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_pairs_write<Loc><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, eps, status);
+    if (simp) k_pairs_write<Loc, true><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, eps, status);
+    else k_pairs_write<Loc, false><<<(unsigned)nchunks, kCompactThreads, 0, st>>>(loc, counts, eps, status);
     return cudaGetLastError();
 }
 
