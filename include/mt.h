@@ -160,6 +160,30 @@ mt_status mt_simplified_components_at(const float *d_f, const uint64_t *d_W, mt_
                                       uint32_t flags, uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
+ * Branch decomposition (Section 2.1: every vertex lies on one branch of the
+ * tree; the CPU implementation of Section 3.1 keeps each branch's vertices in
+ * a list beside its triplets). A minimum u (W[u].s != u, or the root) heads
+ * its own branch; an inner vertex u (W[u] = (u, v), v != u) lies on the
+ * branch of v, the deepest vertex of its component at level f(u).
+ *   d_order    uint32[n], output: every vertex once, grouped by branch --
+ *              branches by ascending id of their minimum -- and each group in
+ *              the vertex order (value, then index; the order of -f with
+ *              MT_SUPERLEVEL), so that each group starts with its minimum.
+ *   d_offsets  uint32[offsets_cap], output: offsets[i] is where group i
+ *              starts in d_order, offsets[nbranches] = n.
+ *   h_nbranches  host; receives the number of branches (= number of minima).
+ *   d_ws       workspace of mt_branches_workspace_bytes(g) bytes (about
+ *              21 bytes per vertex), 256-byte aligned.
+ * Synchronises `stream`. MT_ERR_CAPACITY (true count in *h_nbranches, order
+ * complete, offsets cut off) if offsets_cap < nbranches + 1; MT_ERR_INVALID
+ * if d_W holds an id >= n. flags: 0 or MT_SUPERLEVEL, as for the build.
+ */
+size_t mt_branches_workspace_bytes(mt_grid g);
+mt_status mt_branch_decomposition(const float *d_f, const uint64_t *d_W, mt_grid g, uint32_t flags, uint32_t *d_order,
+                                  uint32_t *d_offsets, uint64_t offsets_cap, uint64_t *h_nbranches, void *d_ws,
+                                  size_t ws_bytes, void *stream);
+
+/*
  * Synchronise `stream` and return (then clear) the workspace status word:
  * MT_OK, MT_ERR_NONFINITE, MT_ERR_TIMEOUT or MT_ERR_CAPACITY.
  */

@@ -16,6 +16,7 @@ Functions
   simplified_pairs(f, W, eps) -> the pairs of persistence >= eps
   simplified_components(f, W, t, eps) -> labels of G_t after filling every
                            branch of persistence < eps up to its saddle
+  branches(f, W)           -> (order, offsets): vertices grouped by branch
 """
 
 from __future__ import annotations
@@ -197,3 +198,28 @@ def simplified_components(f, W: np.ndarray, t: float, eps: float) -> np.ndarray:
     out = lab.copy()
     out[np.isin(lab, reps[short].astype(np.uint32)) & inside] = np.uint32(0xFFFFFFFF)
     return out
+
+
+def branch_of(W: np.ndarray) -> np.ndarray:
+    """The branch of every vertex (Section 2.1): a minimum (W[u].s != u) or the
+    root heads its own branch; an inner vertex u (W[u] = (u, v), v != u) lies
+    on the branch of v, the deepest vertex of its component at level f(u)."""
+    W = np.asarray(W, dtype=np.uint64).ravel()
+    u = np.arange(W.size, dtype=np.uint64)
+    s = W >> np.uint64(32)
+    v = W & np.uint64(0xFFFFFFFF)
+    return np.where((s == u) & (v != u), v, u).astype(np.uint32)
+
+
+def branches(f, W: np.ndarray):
+    """(order, offsets): every vertex grouped by branch, branches by ascending
+    id of their minimum, each group in the vertex order (value, then index) so
+    that it starts with its minimum; offsets[i] = start of group i,
+    offsets[-1] = n. A stable lexicographic sort (numpy)."""
+    g = np.ascontiguousarray(np.asarray(f, dtype=np.float32)).ravel()
+    b = branch_of(W)
+    n = b.size
+    order = np.lexsort((np.arange(n), g, b)).astype(np.uint32)
+    sb = b[order]
+    heads = np.nonzero(np.r_[True, sb[1:] != sb[:-1]])[0].astype(np.uint32)
+    return order, np.r_[heads, np.uint32(n)].astype(np.uint32)

@@ -39,6 +39,9 @@ __all__ = [
     "mt_persistence_pairs_noalloc",
     "mt_simplified_pairs",
     "mt_simplified_components_at",
+    "mt_branches_workspace_bytes",
+    "mt_branch_decomposition",
+    "branches_workspace",
     "BatchPlan",
     "mt_batch_workspace_bytes",
     "mt_batch_prepare",
@@ -105,6 +108,9 @@ _SIGS = {
                             ctypes.c_int32),
     "mt_simplified_components_at": ([_P, _P, Grid, ctypes.c_float, ctypes.c_float, ctypes.c_uint32, _P, _P,
                                      ctypes.c_size_t, _P], ctypes.c_int32),
+    "mt_branches_workspace_bytes": ([Grid], ctypes.c_size_t),
+    "mt_branch_decomposition": ([_P, _P, Grid, ctypes.c_uint32, _P, _P, _U64, _P, _P, ctypes.c_size_t, _P],
+                                ctypes.c_int32),
     "mt_batch_workspace_bytes": ([_P, ctypes.c_uint32], ctypes.c_size_t),
     "mt_batch_prepare": ([_P, _P, ctypes.c_uint32, _P, _P, _P, ctypes.c_size_t, _P, _P], ctypes.c_int32),
     "mt_batch_launch": ([_P, ctypes.c_int, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
@@ -284,6 +290,38 @@ def mt_simplified_components_at(f: torch.Tensor, W: torch.Tensor, t: float, eps:
                                               float(eps), int(flags), _dev(labels, "labels", _I32, n),
                                               _dev(ws, "ws", (torch.uint8,)), ws.numel(), _stream_ptr(stream)),
            "mt_simplified_components_at")
+
+
+def mt_branches_workspace_bytes(grid: Grid) -> int:
+    return int(load().mt_branches_workspace_bytes(grid))
+
+
+def branches_workspace(grid: Grid, device=None) -> torch.Tensor:
+    """A device byte tensor for mt_branch_decomposition on ``grid`` with its
+    status word cleared."""
+    nbytes = mt_branches_workspace_bytes(grid)
+    if nbytes == 0:
+        raise MtError(-1, "mt_branches_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+    ws[:256].zero_()
+    return ws
+
+
+def mt_branch_decomposition(f: torch.Tensor, W: torch.Tensor, flags: int, order: torch.Tensor,
+                            offsets: torch.Tensor, ws: torch.Tensor, stream=None) -> int:
+    """Vertices grouped by branch into ``order`` (int32[n]) with group starts in
+    ``offsets`` (int32[cap], offsets[nbranches] = n); returns the number of
+    branches. Synchronises the stream."""
+    g = grid_of(f)
+    n = f.numel()
+    cap = int(offsets.numel())
+    nb = ctypes.c_uint64(0)
+    code = load().mt_branch_decomposition(_dev(f, "f", (torch.float32,)), _dev(W, "W", _I64, n), g, int(flags),
+                                          _dev(order, "order", _I32, n),
+                                          _dev(offsets, "offsets", _I32) if cap else 0, cap, ctypes.byref(nb),
+                                          _dev(ws, "ws", (torch.uint8,)), ws.numel(), _stream_ptr(stream))
+    _check(code, "mt_branch_decomposition", f" nbranches={nb.value} cap={cap}")
+    return int(nb.value)
 
 
 def mt_persistence_pairs_noalloc(f: torch.Tensor, W: torch.Tensor, pairs: torch.Tensor, stream=None,

@@ -38,7 +38,7 @@ struct Workspace {
 };
 
 // Tracing (mt_trace.cu): phases timed with events on the launching stream.
-enum Phase { kInit = 0, kDescend, kMerge, kRepair, kPairs, kLabels, kBatch, kTile, kPhaseCount };
+enum Phase { kInit = 0, kDescend, kMerge, kRepair, kPairs, kLabels, kBatch, kTile, kBranches, kPhaseCount };
 const char *phase_name(int p);
 void count_launch(unsigned k = 1);
 class PhaseScope {

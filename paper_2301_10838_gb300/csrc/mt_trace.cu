@@ -56,7 +56,7 @@ void drain_locked()
 const char *phase_name(int p)
 {
     static const char *names[kPhaseCount] = {"init", "descend", "merge", "repair", "pairs", "labels",
-                                             "batch", "tile"};
+                                             "batch", "tile", "branches"};
     return (p >= 0 && p < kPhaseCount) ? names[p] : "?";
 }
 
