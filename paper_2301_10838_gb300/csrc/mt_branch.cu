@@ -175,9 +175,11 @@ __global__ void __launch_bounds__(1024) k_scan_apply(uint32_t *a, uint64_t m, co
 
 // Stable scatter of block b's keys and values to the scanned offsets. Warp w
 // owns keys [w * 256, (w + 1) * 256) of the block, read in kSortRows rounds of
-// 32; a key's place is the block's offset for its digit + keys with that digit
-// in earlier warps + in earlier rounds of its warp + on lower lanes of its
-// round.
+// 32; a key's place within the block's run of its digit is the number of keys
+// with that digit in earlier warps, in earlier rounds of its warp and on lower
+// lanes of its round. The keys are first placed in shared memory in that
+// order (digit by digit), then written out in order, so that consecutive
+// threads write consecutive addresses of a digit's run.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *__restrict__ kin,
                                                                 const uint32_t *__restrict__ vin,
                                                                 uint64_t *__restrict__ kout,
@@ -185,13 +187,16 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *
                                                                 uint32_t shift, uint32_t nblocks,
                                                                 const uint32_t *__restrict__ offs)
 {
-    __shared__ uint32_t cnt[kSortWarps][256];  // per-warp digit counts, then running places
-    __shared__ uint32_t base[256];
+    __shared__ uint32_t cnt[kSortWarps][256];  // per-warp digit counts, then running local places
+    __shared__ uint32_t base[256], lstart[256], wtot[kSortWarps];
+    __shared__ uint64_t skey[kSortBlock];
+    __shared__ uint32_t sval[kSortBlock];
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (uint32_t i = threadIdx.x; i < kSortWarps * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
     base[threadIdx.x] = offs[(uint64_t)threadIdx.x * nblocks + blockIdx.x];
     __syncthreads();
-    const uint64_t b0 = (uint64_t)blockIdx.x * kSortBlock + (uint64_t)w * (kSortRows * 32);
+    const uint64_t blk0 = (uint64_t)blockIdx.x * kSortBlock;
+    const uint64_t b0 = blk0 + (uint64_t)w * (kSortRows * 32);
     uint64_t k[kSortRows];
     uint32_t v[kSortRows], peers[kSortRows];
     const uint32_t lt = (1u << lane) - 1u;
@@ -213,12 +218,25 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps, per digit (thread = digit)
+    // thread = digit: the block's count of the digit, its local start
+    // (exclusive scan over digits), and the running places of the warps
     {
-        uint32_t run = base[threadIdx.x];
+        const uint32_t d = threadIdx.x;
+        uint32_t tot = 0;
+        for (uint32_t q = 0; q < kSortWarps; q++) tot += cnt[q][d];
+        uint32_t incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (lane == 31) wtot[w] = incl;
+        __syncthreads();
+        uint32_t run = incl - tot;
+        for (uint32_t q = 0; q < w; q++) run += wtot[q];
+        lstart[d] = run;
         for (uint32_t q = 0; q < kSortWarps; q++) {
-            const uint32_t c = cnt[q][threadIdx.x];
-            cnt[q][threadIdx.x] = run;
+            const uint32_t c = cnt[q][d];
+            cnt[q][d] = run;
             run += c;
         }
     }
@@ -233,9 +251,18 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t *
         if (p && (p & lt) == 0) cnt[w][d] += __popc(p);
         __syncwarp();
         if (p) {
-            kout[pos] = k[r];
-            vout[pos] = v[r];
+            skey[pos] = k[r];
+            sval[pos] = v[r];
         }
+    }
+    __syncthreads();
+    const uint32_t valid = n - blk0 < kSortBlock ? (uint32_t)(n - blk0) : kSortBlock;
+    for (uint32_t j = threadIdx.x; j < valid; j += kSortThreads) {
+        const uint64_t key = skey[j];
+        const uint32_t d = (uint32_t)(key >> shift) & 255u;
+        const uint32_t pos = base[d] + (j - lstart[d]);
+        kout[pos] = key;
+        vout[pos] = sval[j];
     }
 }
 
