@@ -268,9 +268,10 @@ def run_ours(args):
     step_bytes = sum(ab[k] for k in ("tile", "merge", "repair", "pairs", "labels"))
 
     # end to end through the public API with pinned host buffers: every step
-    # copies its field in and its triplets, pairs and labels out. Two sets of
-    # device buffers and separate copy streams let step k's copies overlap
-    # step k+1's kernels.
+    # copies its field in and its triplets, pairs and labels out. Three sets of
+    # device buffers and separate copy streams let step k's copies out overlap
+    # step k+1's kernels, and step k+1's copy in start before step k-1's
+    # copies out have finished.
     e2e = None
     if not args.no_e2e:
         h_f = torch.empty(shape, dtype=torch.float32, pin_memory=True)
@@ -278,29 +279,31 @@ def run_ours(args):
         h_W = torch.empty(n, dtype=torch.int64, pin_memory=True)
         h_lab = torch.empty(n, dtype=torch.int32, pin_memory=True)
         h_pairs = torch.empty((npairs, 2), dtype=torch.int32, pin_memory=True)
+        depth = 3
         bufs = [(f, W, labels, pairs, ws)]
-        bufs.append((torch.empty_like(f), torch.empty_like(W), torch.empty_like(labels), torch.empty_like(pairs),
-                     torch.empty_like(ws)))
+        for _ in range(depth - 1):
+            bufs.append((torch.empty_like(f), torch.empty_like(W), torch.empty_like(labels),
+                         torch.empty_like(pairs), torch.empty_like(ws)))
         s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        done = [torch.cuda.Event(), torch.cuda.Event()]  # buffers of slot i free again
+        done = [torch.cuda.Event() for _ in range(depth)]  # buffers of slot i free again
         for ev in done:
             ev.record(s_out)
         k_e2e = max(3, args.steps)
 
-        loaded = [None, None]
+        loaded = [None] * depth
 
         def prefetch(k):
-            df = bufs[k % 2][0]
-            s_in.wait_event(done[k % 2])
+            df = bufs[k % depth][0]
+            s_in.wait_event(done[k % depth])
             with torch.cuda.stream(s_in):
                 df.copy_(h_f, non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(s_in)
-            loaded[k % 2] = ev
+            loaded[k % depth] = ev
 
         def e2e_step(k, last):
-            df, dW, dl, dp, dws = bufs[k % 2]
-            s_cmp.wait_event(loaded[k % 2])
+            df, dW, dl, dp, dws = bufs[k % depth]
+            s_cmp.wait_event(loaded[k % depth])
             mt.mt_build_triplets(df, dW, dws, stream=s_cmp)
             mt.mt_components_at(df, dW, t_thr, dl, dws, stream=s_cmp)
             built = torch.cuda.Event()
@@ -317,7 +320,7 @@ def run_ours(args):
             s_out.wait_event(paired)
             with torch.cuda.stream(s_out):
                 h_pairs[:np_].copy_(dp[:np_], non_blocking=True)
-                done[k % 2].record(s_out)
+                done[k % depth].record(s_out)
 
         prefetch(0)
         e2e_step(0, True)

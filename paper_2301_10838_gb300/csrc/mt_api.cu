@@ -64,6 +64,46 @@ static mt_status grid_n(mt_grid g, uint64_t &n)
     return MT_OK;
 }
 
+// Small results (pair count, roots, status word) come back to the host
+// through mapped pinned memory written by a one-thread kernel, not through a
+// device-to-host copy: a copy would queue on the copy engine behind any large
+// download another stream has in flight (such as the caller's copy of a
+// previous field's triplets) and stall the call for its whole duration.
+// One buffer per host thread, allocated on first use and kept.
+__global__ void k_readback(const uint64_t *meta, const uint32_t *status, volatile uint64_t *out)
+{
+    if (meta) {
+        out[0] = meta[0];
+        out[1] = meta[1];
+        out[2] = meta[2];
+    }
+    out[3] = *status;
+}
+
+// out[0..2] = meta (if given), out[3] = status word; synchronises s
+static cudaError_t readback(const uint64_t *meta, const uint32_t *status, cudaStream_t s, uint64_t out[4])
+{
+    thread_local uint64_t *h = nullptr, *d = nullptr;
+    if (!h) {
+        void *hp = nullptr, *dp = nullptr;
+        cudaError_t e = cudaHostAlloc(&hp, 64, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaHostGetDevicePointer(&dp, hp, 0)) != cudaSuccess) {
+            cudaFreeHost(hp);
+            return e;
+        }
+        h = static_cast<uint64_t *>(hp), d = static_cast<uint64_t *>(dp);
+    }
+    k_readback<<<1, 1, 0, s>>>(meta, status, d);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    const volatile uint64_t *vh = h;
+    for (int i = 0; i < 4; i++) out[i] = vh[i];
+    return cudaSuccess;
+}
+
 mt_status status_from_bits(uint32_t bits)
 {
     if (bits & ST_NONFINITE) return MT_ERR_NONFINITE;
@@ -138,12 +178,9 @@ mt_status mt_persistence_pairs(const float *d_f, const uint64_t *d_W, mt_grid g,
     if (!carve_workspace(d_ws, ws_bytes, n, ws)) return MT_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (launch_pairs(d_W, n, d_pairs, cap, ws, s) != cudaSuccess) return MT_ERR_CUDA;
-    uint64_t meta[3] = {0, 0, 0};
-    uint32_t bits = 0;
-    if (cudaMemcpyAsync(meta, ws.meta, sizeof(meta), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MT_ERR_CUDA;
-    if (cudaMemcpyAsync(&bits, ws.status, sizeof(bits), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return MT_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return MT_ERR_CUDA;
+    uint64_t meta[4];
+    if (readback(ws.meta, ws.status, s, meta) != cudaSuccess) return MT_ERR_CUDA;
+    const uint32_t bits = (uint32_t)meta[3];
     if (bits) return status_from_bits(bits);
     *h_npairs = meta[0];
     if (h_root) *h_root = meta[1] == 1 ? (uint32_t)meta[2] : 0xFFFFFFFFu;
@@ -166,12 +203,9 @@ mt_status mt_simplified_pairs(const float *d_f, const uint64_t *d_W, mt_grid g, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const float sg = (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f;
     if (launch_pairs(d_W, n, d_pairs, cap, ws, s, d_f, sg, eps) != cudaSuccess) return MT_ERR_CUDA;
-    uint64_t meta[3] = {0, 0, 0};
-    uint32_t bits = 0;
-    if (cudaMemcpyAsync(meta, ws.meta, sizeof(meta), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MT_ERR_CUDA;
-    if (cudaMemcpyAsync(&bits, ws.status, sizeof(bits), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return MT_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return MT_ERR_CUDA;
+    uint64_t meta[4];
+    if (readback(ws.meta, ws.status, s, meta) != cudaSuccess) return MT_ERR_CUDA;
+    const uint32_t bits = (uint32_t)meta[3];
     if (bits) return status_from_bits(bits);
     *h_npairs = meta[0];
     if (h_root) *h_root = meta[1] == 1 ? (uint32_t)meta[2] : 0xFFFFFFFFu;
@@ -225,9 +259,9 @@ mt_status mt_sync_status(void *d_ws, void *stream)
 {
     if (!d_ws || ((uintptr_t)d_ws & 255)) return MT_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    uint32_t bits = 0;
-    if (cudaMemcpyAsync(&bits, d_ws, sizeof(bits), cudaMemcpyDeviceToHost, s) != cudaSuccess) return MT_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return MT_ERR_CUDA;
+    uint64_t rb[4];
+    if (readback(nullptr, static_cast<const uint32_t *>(d_ws), s, rb) != cudaSuccess) return MT_ERR_CUDA;
+    const uint32_t bits = (uint32_t)rb[3];
     if (bits && cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) != cudaSuccess) return MT_ERR_CUDA;
     return status_from_bits(bits);
 }
