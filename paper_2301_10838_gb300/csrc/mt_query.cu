@@ -54,11 +54,17 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t b0 = local * kCompactChunk + (uint64_t)warp * (kCompactRows * 32);
     uint32_t c = 0;
-#pragma unroll 4
+    // all rows are loaded before any is used, so that their loads overlap
+    uint64_t Tr[kCompactRows];
+#pragma unroll
     for (int r = 0; r < kCompactRows; r++) {
         const uint64_t u = b0 + (uint64_t)r * 32 + lane;
-        if (u >= n) break;
-        const uint64_t T = W[u];
+        Tr[r] = u < n ? W[u] : tri_pack((uint32_t)u, (uint32_t)u + 1);  // past the end: neither pair nor root
+    }
+#pragma unroll
+    for (int r = 0; r < kCompactRows; r++) {
+        const uint64_t u = b0 + (uint64_t)r * 32 + lane;
+        const uint64_t T = Tr[r];
         if (tri_s(T) != (uint32_t)u) {
             c += keep_pair<SIMP>(fd, T, (uint32_t)u, eps);
         } else if (tri_v(T) == (uint32_t)u) {
