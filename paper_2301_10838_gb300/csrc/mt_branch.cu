@@ -406,7 +406,8 @@ mt_status mt_branch_decomposition(const float *d_f, const uint64_t *d_W, mt_grid
     PhaseScope ps(kBranches, st);
     if (cudaMemcpyAsync(bw.orand, init, sizeof(init), cudaMemcpyHostToDevice, st) != cudaSuccess) return MT_ERR_CUDA;
     // the 64-bit keys go to k0 and the values to d_order; every pass swaps
-    const unsigned kgrid = (unsigned)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+    const uint64_t kmax = (uint64_t)device_sms() * 16;  // grid-stride: 16 CTAs of 256 per SM
+    const unsigned kgrid = (unsigned)((n + 255) / 256 < kmax ? (n + 255) / 256 : kmax);
     k_branch_keys<<<kgrid, 256, 0, st>>>(Field{d_f, sg}, d_W, (uint32_t)n, bw.k0, d_order, bw.orand, ws.status);
     count_launch();
     unsigned long long orand[2];
