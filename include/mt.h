@@ -307,7 +307,7 @@ mt_status mt_persistence_pairs_noalloc(const float *d_f, const uint64_t *d_W, mt
 
 /* ------------------------------------------------------------- tracing
  * Not part of the paper's method: diagnostics for benchmarks and profiling.
- * When enabled, every step (init, descend, merge, repair, pairs, labels, ...)
+ * When enabled, every step (tile, merge, repair, pairs, labels, branches)
  * is bracketed by CUDA events on the stream it runs on; mt_trace_read waits
  * for the recorded events and returns the accumulated device time per step.
  */

@@ -40,7 +40,6 @@ bool carve_workspace(void *base, size_t bytes, uint64_t n, Workspace &ws)
     if (!base || ((uintptr_t)base & 255) || bytes < workspace_bytes(n)) return false;
     char *p = static_cast<char *>(base);
     ws.status = reinterpret_cast<uint32_t *>(p);
-    ws.more = reinterpret_cast<uint32_t *>(p + 4);
     ws.meta = reinterpret_cast<uint64_t *>(p + 256);
     ws.counts = reinterpret_cast<uint32_t *>(p + 512);
     ws.nchunks = (n + kCompactChunk - 1) / kCompactChunk;

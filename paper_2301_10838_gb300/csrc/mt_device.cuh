@@ -25,7 +25,6 @@ constexpr uint32_t kChaseLimit = 1u << 24;
 __device__ __forceinline__ uint32_t tri_s(uint64_t w) { return (uint32_t)(w >> 32); }
 __device__ __forceinline__ uint32_t tri_v(uint64_t w) { return (uint32_t)w; }
 __device__ __forceinline__ uint64_t tri_pack(uint32_t s, uint32_t v) { return ((uint64_t)s << 32) | v; }
-__device__ __forceinline__ bool tri_is_root(uint64_t w, uint32_t u) { return w == tri_pack(u, u); }
 
 // a before b in the total order (value, index)
 __device__ __forceinline__ bool before(float fa, uint32_t a, float fb, uint32_t b)
@@ -136,26 +135,13 @@ __device__ __forceinline__ bool merge(uint64_t *W, const Field f, uint32_t S, ui
 // vertex of x's component below S. Hops while the link's saddle s' satisfies
 // s' <= S in the vertex order and returns the vertex where it stops (the
 // printed algorithm returns one hop further; the vertex itself is the one
-// the definition asks for).
-__device__ __forceinline__ uint32_t representative(const uint64_t *W, const Field f, uint32_t x, uint32_t S, float fS,
-                                                   uint32_t &steps)
-{
-    for (;;) {
-        const uint64_t T = ld_tri(W + x);
-        const uint32_t s = tri_s(T), t = tri_v(T);
-        if (s == x && t == x) return x;
-        if (s != S && !before(f[s], s, fS, S)) return x;
-        x = t;
-        if (++steps > kChaseLimit) return x;
-    }
-}
-
-// The same chase with ordinary (L1-cacheable) loads, for passes in which the
-// entries only ever move further along their own chains (repair): a stale
-// copy then still leads to the same representative. The triplet of the next
-// vertex is loaded together with the value of the current saddle, before the
-// level test decides whether it is needed, so that a hop costs one memory
-// latency instead of two (the extra load reads a valid entry either way).
+// the definition asks for). Ordinary (L1-cacheable) loads: it serves passes
+// in which the entries only ever move further along their own chains
+// (repair), where a stale copy still leads to the same representative. The
+// triplet of the next vertex is loaded together with the value of the
+// current saddle, before the level test decides whether it is needed, so that
+// a hop costs one memory latency instead of two (the extra load reads a valid
+// entry either way).
 __device__ __forceinline__ uint32_t representative_cached(const uint64_t *W, const Field f, uint32_t x, uint32_t S,
                                                           float fS, uint32_t &steps)
 {

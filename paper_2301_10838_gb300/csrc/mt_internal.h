@@ -30,7 +30,6 @@ struct FieldDesc {
 // Views into the caller's workspace (layout fixed by carve_workspace).
 struct Workspace {
     uint32_t *status;  // status bits (ST_*)
-    uint32_t *more;    // "another round needed" flag of iterative kernels
     uint64_t *meta;    // [0] npairs, [1] number of roots, [2] root
     uint32_t *faces;   // per tile: tile-local tops of the cross-edge ends, or null vertex
     uint32_t *counts;  // per-chunk counts, then exclusive offsets in place
@@ -38,7 +37,7 @@ struct Workspace {
 };
 
 // Tracing (mt_trace.cu): phases timed with events on the launching stream.
-enum Phase { kInit = 0, kDescend, kMerge, kRepair, kPairs, kLabels, kBatch, kTile, kBranches, kPhaseCount };
+enum Phase { kTile = 0, kMerge, kRepair, kPairs, kLabels, kBranches, kPhaseCount };
 const char *phase_name(int p);
 void count_launch(unsigned k = 1);
 class PhaseScope {

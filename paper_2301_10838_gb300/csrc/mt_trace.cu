@@ -55,8 +55,7 @@ void drain_locked()
 
 const char *phase_name(int p)
 {
-    static const char *names[kPhaseCount] = {"init", "descend", "merge", "repair", "pairs", "labels",
-                                             "batch", "tile", "branches"};
+    static const char *names[kPhaseCount] = {"tile", "merge", "repair", "pairs", "labels", "branches"};
     return (p >= 0 && p < kPhaseCount) ? names[p] : "?";
 }
 
