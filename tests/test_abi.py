@@ -90,6 +90,35 @@ def test_argument_errors_need_no_gpu(lib):
                                     ctypes.c_void_p(256), nbytes, None) == -1
 
 
+def test_simplification_and_branch_argument_errors_need_no_gpu(lib):
+    """The simplification and branch-decomposition calls reject bad arguments
+    (NaN thresholds, null outputs, bad flags, short workspaces) before any
+    device work."""
+    g = mt.Grid(4, 4, 4)
+    nbytes = lib.mt_workspace_bytes(g)
+    P = ctypes.c_void_p(256)
+    npairs = ctypes.c_uint64(0)
+    nan = float("nan")
+    assert lib.mt_simplified_pairs(P, P, g, nan, 0, P, 8, ctypes.byref(npairs), None, P, nbytes, None) == -1
+    assert lib.mt_simplified_pairs(P, P, g, 0.5, 4, P, 8, ctypes.byref(npairs), None, P, nbytes, None) == -1
+    assert lib.mt_simplified_pairs(P, P, g, 0.5, 0, P, 8, None, None, P, nbytes, None) == -1
+    assert lib.mt_simplified_components_at(P, P, g, nan, 0.1, 0, P, P, nbytes, None) == -1
+    assert lib.mt_simplified_components_at(P, P, g, 0.5, nan, 0, P, P, nbytes, None) == -1
+    assert lib.mt_simplified_components_at(P, P, g, 0.5, 0.1, 0, None, P, nbytes, None) == -1
+    bbytes = lib.mt_branches_workspace_bytes(g)
+    assert bbytes > 0 and bbytes % 256 == 0
+    big = lib.mt_branches_workspace_bytes(mt.Grid(1024, 1024, 1024))
+    assert big >= 20 * 1024 ** 3  # two 64-bit key arrays and one 32-bit value array per vertex
+    assert lib.mt_branches_workspace_bytes(mt.Grid(0, 1, 1)) == 0
+    assert lib.mt_branches_workspace_bytes(mt.Grid(65536, 65536, 1)) == 0
+    nb = ctypes.c_uint64(0)
+    assert lib.mt_branch_decomposition(P, P, g, 0, P, P, 65, ctypes.byref(nb), P, bbytes - 1, None) == -1
+    assert lib.mt_branch_decomposition(P, P, g, 0, None, P, 65, ctypes.byref(nb), P, bbytes, None) == -1
+    assert lib.mt_branch_decomposition(P, P, g, 2, P, P, 65, ctypes.byref(nb), P, bbytes, None) == -1
+    assert lib.mt_branch_decomposition(P, P, mt.Grid(65536, 65536, 1), 0, P, P, 65, ctypes.byref(nb), P, bbytes,
+                                       None) == -2
+
+
 def test_library_is_sm103a_only():
     """The build passes exactly one -gencode, for sm_103a."""
     assert mtbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -131,3 +131,25 @@ def test_simplification_limits():
     big = oracle.simplified_components(f, W, t, np.inf)
     kept = np.unique(big[big != FFFF])
     assert list(kept) == [int(roots[0])] or (len(kept) == 0 and lab[roots[0]] == FFFF)
+
+
+def test_eps_equal_to_a_persistence_keeps_that_pair():
+    """A pair whose persistence equals eps is kept (p >= eps); its component
+    stays in G_t. The filled field agrees at exactly that boundary."""
+    rng = np.random.default_rng(41)
+    for _ in range(40):
+        f = rng.integers(0, 7, size=(4, 5, 5)).astype(np.float32)
+        W = oracle.merge_tree(f)
+        p, _ = oracle.pairs(W)
+        if len(p) == 0:
+            continue
+        pers = oracle.persistence(f, W, p[:, 0])
+        eps = float(pers[rng.integers(0, len(pers))])
+        kept = oracle.simplified_pairs(f, W, eps)
+        assert np.array_equal(kept, p[pers >= np.float32(eps)])
+        if eps > 0:
+            assert len(kept) >= 1 and np.any(oracle.persistence(f, W, kept[:, 0]) == np.float32(eps))
+        t = float(rng.uniform(f.min(), f.max()))
+        g = _filled(f, brute_merge_tree(f), eps)
+        lab = oracle.simplified_components(f, W, t, eps)
+        assert np.array_equal(lab != FFFF, g.ravel() <= np.float32(t))
