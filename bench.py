@@ -129,9 +129,9 @@ def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 32)) -> dict:
       repair  read + write W (16n)
       pairs   scan W (8n) + write pairs (8 npairs)
       labels  read f (4n) + W (8n), write labels (4n)
-    E' = E - (n - #minima) (edges that are not steepest-descent seeds, the
-    survey's model) and C the edges between tiles; tile + merge together are
-    the model's 12n + 16E'.
+    E' = E - (n - #minima) (edges that are not steepest-descent seeds: the
+    per-edge cost of the edge loop of Algorithm 1) and C the edges between
+    tiles; tile + merge together are 12n + 16E'.
     """
     nz, ny, nx = shape
     tz, ty, tx = tile
