@@ -188,6 +188,19 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ ours
+def field_digest(f) -> str:
+    """sha256 of the field's bytes (rank 0's field), so that a run can be
+    tied to the exact input; read back in 256 MiB slices."""
+    import hashlib
+
+    h = hashlib.sha256()
+    flat = f.reshape(-1)
+    step = 1 << 26
+    for i in range(0, flat.numel(), step):
+        h.update(flat[i:i + step].cpu().numpy().tobytes())
+    return h.hexdigest()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -209,6 +222,7 @@ def run_ours(args):
     n = f.numel()
     shape = tuple(f.shape)
     t_thr = float(f.reshape(-1)[:: 4099].float().median())
+    field_sha = field_digest(f)
     W = torch.empty(n, dtype=torch.int64, device=dev)
     ws = mt.workspace(mt.grid_of(f), device=dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
@@ -365,6 +379,7 @@ def run_ours(args):
                 "workload": WORKLOAD if side == 1024 else f"{WORKLOAD}@{side}^3",
                 "grid": [shape[2], shape[1], shape[0]],
                 "field": "exp(0.8 g), g unit-variance GRF P(k)~k^-2, float32, seed 1+rank",
+                "field_sha256": field_sha,
                 "step": "mt_build_triplets + mt_persistence_pairs + mt_components_at(median)",
                 "threshold": t_thr,
                 "npairs": npairs,
