@@ -380,18 +380,10 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
         s_boff[NB + 1] = run;
     }
     __syncthreads();
-    for (uint32_t l0 = 0; l0 < TV; l0 += NT) {
-        const uint32_t l = l0 + threadIdx.x;
-        const bool ok_l = valid(l);
-        const uint32_t b = !ok_l ? 0xFFFFFFFFu : tid_v(vT[l]) == l ? (uint32_t)NB : bucket_of(K[l]);
-        const uint32_t peers = __match_any_sync(0xffffffffu, b);
-        if (ok_l) {
-            const uint32_t leader = __ffs(peers) - 1;
-            uint32_t pos = 0;
-            if (lane == leader) pos = atomicAdd(&s_bcur[b], __popc(peers));
-            pos = __shfl_sync(peers, pos, leader);
-            vlist[pos + __popc(peers & ((1u << lane) - 1u))] = (uint16_t)l;
-        }
+    for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+        if (!valid(l)) continue;
+        const uint32_t b = tid_v(vT[l]) == l ? (uint32_t)NB : bucket_of(K[l]);
+        vlist[atomicAdd(&s_bcur[b], 1u)] = (uint16_t)l;  // order within a segment is free
     }
     __syncthreads();
 
