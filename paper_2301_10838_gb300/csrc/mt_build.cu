@@ -203,7 +203,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     uint32_t *hist = reinterpret_cast<uint32_t *>(hlev);          // key histogram (before the rounds)
     __shared__ uint8_t s_bmap[BINS];                              // histogram bin -> bucket
     __shared__ uint32_t s_kmin, s_kmax, s_nvalid, s_warp[NT / 32];
-    __shared__ uint32_t s_boff[NB + 2], s_bcur[NB + 1];
+    __shared__ uint32_t s_boff[NB + 2], s_bcur[NB + 1], s_thr[NB];
 
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
@@ -326,6 +326,19 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     __syncthreads();
     volatile uint32_t *vT = T;
     auto bucket_of = [&](uint32_t k) { return (uint32_t)s_bmap[bin_of(k)]; };
+    // The bucket of a key grows with the key, so "in bucket b or later" is
+    // k >= s_thr[b], the smallest key of bucket b or after (kmax + 1 if none):
+    // one compare in the shortcut climbs instead of the bin lookup. Read
+    // only after the barriers that end step 4.
+    if (threadIdx.x < (uint32_t)NB) {
+        uint32_t lo = kmin_t, hi = s_kmax + 1u;
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            if (bucket_of(mid) >= threadIdx.x) hi = mid;
+            else lo = mid + 1;
+        }
+        s_thr[threadIdx.x] = lo;
+    }
     // Spare bits of an inner vertex's triplet (ids take IDB of each 16-bit
     // half) carry its cross mask: bit d is set when its neighbour in direction
     // d (-x, -y, -z, +x, +y, +z) is lower and descends to another minimum.
@@ -401,7 +414,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
             if ((sc >> IDB) == (uint32_t)b) return x;
             for (uint32_t h = 0; h < (uint32_t)TV; h++) {
                 const uint32_t w = vT[x];
-                if (w == sm_pack(x, x) || bucket_of(K[sm_s(w)]) >= (uint32_t)b) break;
+                if (w == sm_pack(x, x) || K[sm_s(w)] >= s_thr[b]) break;
                 x = sm_v(w);
             }
             vSC[m] = (uint16_t)(((uint32_t)b << IDB) | x);
