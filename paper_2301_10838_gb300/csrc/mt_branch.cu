@@ -49,7 +49,9 @@ __global__ void __launch_bounds__(256) k_branch_keys(const Field f, const uint64
 {
     unsigned long long o = 0, a = ~0ull;
     bool bad = false;
-    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    // 64-bit index: near n = 2^32 a 32-bit index plus the stride would wrap
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = (uint32_t)i;
         const uint64_t T = W[u];
         const uint32_t s = tri_s(T), v = tri_v(T);
         if (s >= n || v >= n) bad = true;
