@@ -91,3 +91,102 @@ def test_planted_mistake_is_caught(name, tmp_path, monkeypatch):
     assert SOURCE.count(old) == 1, name
     _with_source(SOURCE.replace(old, new), tmp_path, monkeypatch)
     assert not _pins_pass(), f"the pins did not catch: {name}"
+
+
+# ---- the numpy layer of the oracle: simplification and branches
+
+def _simplify_pins_pass() -> bool:
+    from test_oracle_simplify import FFFF, _cases, _filled
+
+    for ties in (False, True):
+        for f, t, eps in _cases(60, 101 + ties, ties):
+            W = oracle.merge_tree(f)
+            g = _filled(f, brute_merge_tree(f), eps)
+            lab = oracle.simplified_components(f, W, t, eps)
+            if not np.array_equal(lab != FFFF, g.ravel() <= np.float32(t)):
+                return False
+            # eps equal to a representative's persistence keeps its component
+            lab0 = oracle.components(f, t)
+            reps = [int(r) for r in np.unique(lab0[lab0 != FFFF]) if (int(W[r]) >> 32) != int(r)]
+            if reps:
+                e1 = float(oracle.persistence(f, W, [reps[0]])[0])
+                lab1 = oracle.simplified_components(f, W, t, e1)
+                g1 = _filled(f, brute_merge_tree(f), e1)
+                if not np.array_equal(lab1 != FFFF, g1.ravel() <= np.float32(t)) or np.any(lab1[lab0 == reps[0]] == FFFF):
+                    return False
+            # eps equal to a persistence keeps that pair
+            p, _ = oracle.pairs(W)
+            if len(p):
+                pers = oracle.persistence(f, W, p[:, 0])
+                e0 = float(pers[0])
+                if not np.array_equal(oracle.simplified_pairs(f, W, e0), p[pers >= np.float32(e0)]):
+                    return False
+    return True
+
+
+def _branch_pins_pass() -> bool:
+    from test_oracle_branches import _brute_branch
+
+    rng = np.random.default_rng(9)
+    for _ in range(40):
+        shape = tuple(int(x) for x in rng.integers(1, 5, size=3))
+        f = rng.integers(0, 4, size=shape).astype(np.float32)
+        W = oracle.merge_tree(f)
+        if not np.array_equal(oracle.branch_of(W), _brute_branch(f)):
+            return False
+        order, offsets = oracle.branches(f, W)
+        flat = [float(x) for x in f.ravel()]
+        b = oracle.branch_of(W)
+        if [int(x) for x in order] != sorted(range(f.size), key=lambda i: (int(b[i]), flat[i], i)):
+            return False
+    return True
+
+
+def test_numpy_layer_passes_unmodified():
+    assert _simplify_pins_pass() and _branch_pins_pass()
+
+
+def _persistence_from_target(f, W, u):
+    g = np.ascontiguousarray(np.asarray(f, dtype=np.float32)).ravel()
+    u = np.asarray(u, dtype=np.int64)
+    v = (np.asarray(W, dtype=np.uint64).ravel()[u] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    return g[v] - g[u]
+
+
+def _simplified_components_le(f, W, t, eps):
+    lab = oracle.components(f, t)
+    inside = lab != np.uint32(0xFFFFFFFF)
+    reps = np.unique(lab[inside]).astype(np.int64)
+    if len(reps) == 0:
+        return lab
+    Wf = np.asarray(W, dtype=np.uint64).ravel()
+    s = (Wf[reps] >> np.uint64(32)).astype(np.int64)
+    short = (s != reps) & (oracle.persistence(f, Wf, reps) <= np.float32(eps))  # planted: <= for <
+    out = lab.copy()
+    out[np.isin(lab, reps[short].astype(np.uint32)) & inside] = np.uint32(0xFFFFFFFF)
+    return out
+
+
+def _branch_of_self(W):
+    return np.arange(np.asarray(W).size, dtype=np.uint32)  # planted: every vertex heads its own branch
+
+
+def _branches_descending(f, W):
+    g = np.ascontiguousarray(np.asarray(f, dtype=np.float32)).ravel()
+    b = oracle.branch_of(W)
+    order = np.lexsort((np.arange(b.size), -g, b)).astype(np.uint32)  # planted: values descending
+    sb = b[order]
+    heads = np.nonzero(np.r_[True, sb[1:] != sb[:-1]])[0].astype(np.uint32)
+    return order, np.r_[heads, np.uint32(b.size)].astype(np.uint32)
+
+
+@pytest.mark.parametrize("name,attr,fake,pins", [
+    ("persistence from the target, not the saddle", "persistence", _persistence_from_target, "simplify"),
+    ("a pair at exactly eps dropped", "simplified_components", _simplified_components_le, "simplify"),
+    ("every vertex its own branch", "branch_of", _branch_of_self, "branches"),
+    ("groups in descending value", "branches", _branches_descending, "branches"),
+])
+def test_numpy_layer_mistake_is_caught(name, attr, fake, pins, monkeypatch):
+    monkeypatch.setattr(oracle, attr, fake)
+    ok = _simplify_pins_pass() if pins == "simplify" else _branch_pins_pass()
+    assert not ok, f"the pins did not catch: {name}"

@@ -153,3 +153,14 @@ def test_eps_equal_to_a_persistence_keeps_that_pair():
         g = _filled(f, brute_merge_tree(f), eps)
         lab = oracle.simplified_components(f, W, t, eps)
         assert np.array_equal(lab != FFFF, g.ravel() <= np.float32(t))
+        # a component whose representative's persistence is exactly eps stays
+        lab0 = oracle.components(f, t)
+        for r in np.unique(lab0[lab0 != FFFF]):
+            r = int(r)
+            if (int(W[r]) >> 32) == r:
+                continue
+            er = float(oracle.persistence(f, W, [r])[0])
+            lab_r = oracle.simplified_components(f, W, t, er)
+            assert np.all(lab_r[lab0 == r] == r)
+            gr = _filled(f, brute_merge_tree(f), er)
+            assert np.array_equal(lab_r != FFFF, gr.ravel() <= np.float32(t))
