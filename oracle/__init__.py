@@ -9,7 +9,10 @@ never does.
 
 Functions
   merge_tree(f)            -> W   (uint64[n], W[u] = (s << 32) | v)
-  sort_order(f), sweep(f, order) the two phases of merge_tree, for timing
+  sort_order(f), sweep(f, order) the two phases of merge_tree, for timing;
+                           sort_order sorts 64-bit order keys with numpy
+                           (method="keys") or runs qsort with a comparison
+                           function (method="qsort"): the same order
   pairs(W)                 -> (pairs uint32[k, 2] = (minimum, saddle), roots)
   components(f, t)         -> labels (uint32[n]; 0xFFFFFFFF outside G_t)
   point_triplet(f, u, budget) -> W[u] or None if the query exceeds budget
@@ -64,6 +67,7 @@ def _load():
             U32, U64 = ctypes.c_uint32, ctypes.c_uint64
             for name, args in {
                 "oracle_sort_order": [P, U32, U32, U32, P],
+                "oracle_order_keys": [P, U32, U32, U32, P],
                 "oracle_sweep": [P, U32, U32, U32, P, P],
                 "oracle_merge_tree": [P, U32, U32, U32, P],
                 "oracle_pairs": [P, U64, P, U64, P, P, P],
@@ -98,11 +102,27 @@ def _check(code: int):
         raise OracleError(code)
 
 
-def sort_order(f) -> np.ndarray:
+def sort_order(f, method: str = "keys") -> np.ndarray:
+    """Vertex ids in the order (value, linear index) of Section 2.1's sweep.
+
+    method "keys": oracle_order_keys writes one 64-bit key per vertex whose
+    unsigned order is that order, numpy sorts the keys (a library sort of
+    plain integers) and their low halves are the ids. method "qsort": the C
+    library's qsort with a comparison function on (value, index). Both give
+    the same order; the second takes minutes at 1024^3.
+    """
     f, nx, ny, nz = _field(f)
-    order = np.empty(f.size, dtype=np.uint32)
-    _check(_load().oracle_sort_order(_ptr(f), nx, ny, nz, _ptr(order)))
-    return order
+    if method == "qsort":
+        order = np.empty(f.size, dtype=np.uint32)
+        _check(_load().oracle_sort_order(_ptr(f), nx, ny, nz, _ptr(order)))
+        return order
+    if method != "keys":
+        raise ValueError(method)
+    keys = np.empty(f.size, dtype=np.uint64)
+    _check(_load().oracle_order_keys(_ptr(f), nx, ny, nz, _ptr(keys)))
+    keys.sort()
+    np.bitwise_and(keys, np.uint64(0xFFFFFFFF), out=keys)
+    return keys.astype(np.uint32)
 
 
 def sweep(f, order: np.ndarray) -> np.ndarray:
@@ -113,31 +133,38 @@ def sweep(f, order: np.ndarray) -> np.ndarray:
     return W
 
 
-def merge_tree(f) -> np.ndarray:
-    """Triplet merge tree W[u] = (s << 32) | v of the sublevel sets of f."""
-    f, nx, ny, nz = _field(f)
-    W = np.empty(f.size, dtype=np.uint64)
-    _check(_load().oracle_merge_tree(_ptr(f), nx, ny, nz, _ptr(W)))
-    return W
+def merge_tree(f, method: str = "keys") -> np.ndarray:
+    """Triplet merge tree W[u] = (s << 32) | v of the sublevel sets of f:
+    sort the vertices (``sort_order``), then sweep them (``sweep``)."""
+    return sweep(f, sort_order(f, method))
 
 
 def pairs(W: np.ndarray):
-    """(pairs[k, 2] = (minimum u, saddle s) by ascending u, roots list)."""
+    """(pairs[k, 2] = (minimum u, saddle s) by ascending u, roots list).
+
+    oracle_pairs runs twice: once to count, once to write exactly that many
+    pairs (no n-sized temporaries, so that 1024^3 trees fit in host memory).
+    """
     W = np.ascontiguousarray(W, dtype=np.uint64).ravel()
     n = W.size
-    s = (W >> np.uint64(32)).astype(np.uint64)
-    cap = int(np.count_nonzero(s != np.arange(n, dtype=np.uint64)))
-    out = np.empty((max(cap, 1), 2), dtype=np.uint32)
+    lib = _load()
     npairs = ctypes.c_uint64(0)
     nroots = ctypes.c_uint64(0)
     root = ctypes.c_uint32(0xFFFFFFFF)
-    _check(_load().oracle_pairs(_ptr(W), n, _ptr(out), cap, ctypes.byref(npairs), ctypes.byref(nroots),
-                                ctypes.byref(root)))
+    code = lib.oracle_pairs(_ptr(W), n, None, 0, ctypes.byref(npairs), ctypes.byref(nroots), ctypes.byref(root))
+    if code not in (0, -4):
+        _check(code)
     k = int(npairs.value)
-    v = W & np.uint64(0xFFFFFFFF)
-    roots = np.nonzero((s == np.arange(n, dtype=np.uint64)) & (v == np.arange(n, dtype=np.uint64)))[0]
-    assert len(roots) == int(nroots.value)
-    return out[:k].copy(), roots.astype(np.uint32)
+    out = np.empty((max(k, 1), 2), dtype=np.uint32)
+    _check(lib.oracle_pairs(_ptr(W), n, _ptr(out), k, ctypes.byref(npairs), ctypes.byref(nroots),
+                            ctypes.byref(root)))
+    if int(nroots.value) == 1:
+        roots = np.array([root.value], dtype=np.uint32)
+    else:  # a forest (never for a grid): list every root
+        u = np.arange(n, dtype=np.uint64)
+        roots = np.nonzero(((W >> np.uint64(32)) == u) & ((W & np.uint64(0xFFFFFFFF)) == u))[0].astype(np.uint32)
+        assert len(roots) == int(nroots.value)
+    return out[:k].copy() if k else out[:0].copy(), roots
 
 
 def components(f, t: float) -> np.ndarray:

@@ -254,3 +254,35 @@ def test_split_phases_equal_whole():
     flat = f.ravel()
     keys = list(zip(flat[order].tolist(), order.tolist()))
     assert keys == sorted(keys)
+
+
+def test_key_sort_equals_comparison_sort():
+    """The two sorts of the sweep give the same order: 64-bit keys sorted by
+    numpy and qsort with a comparison on (value, index). Inputs with heavy
+    ties, signed zeros, negative values and subnormals; the qsort order is
+    itself pinned by the brute-force trees above."""
+    rng = np.random.default_rng(3)
+    pool = np.array([-0.0, 0.0, -1.5, 2.0, -2.5, 1e-45, -1e-45, -3.4e38, 3.4e38], np.float32)
+    for i in range(200):
+        shape = tuple(int(x) for x in rng.integers(1, 9, size=3))
+        if i % 3 == 0:
+            f = rng.choice(pool, size=shape)
+        elif i % 3 == 1:
+            f = rng.integers(-3, 3, size=shape).astype(np.float32)
+        else:
+            f = rng.standard_normal(shape).astype(np.float32)
+        a = oracle.sort_order(f, "keys")
+        b = oracle.sort_order(f, "qsort")
+        assert np.array_equal(a, b), shape
+        # and the order is the Python tuple sort by (value, index), with -0 == +0
+        flat = [float(x) for x in f.ravel()]
+        assert [int(x) for x in a] == sorted(range(f.size), key=lambda j: (flat[j], j))
+
+
+def test_order_keys_non_finite_refused():
+    for bad in (np.nan, np.inf, -np.inf):
+        f = np.zeros((2, 2, 2), np.float32)
+        f[1, 0, 1] = bad
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.sort_order(f, "keys")
+        assert e.value.code == -3

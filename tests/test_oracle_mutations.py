@@ -33,6 +33,11 @@ MUTATIONS = {
                                              "    if (a->idx < b->idx) return 1;\n    if (a->idx > b->idx) return -1;"),
     "strict sublevel set": ("        if (!(f[u] <= t)) continue;\n        uint64_t nb[6];",
                             "        if (!(f[u] < t)) continue;\n        uint64_t nb[6];"),
+    "key keeps -0 below +0": ("        if (x == 0.0f) x = 0.0f; /* -0 -> +0 */\n", ""),
+    "key of a negative value not flipped": ("uint32_t m = (b & 0x80000000u) ? ~b : (b | 0x80000000u);",
+                                           "uint32_t m = (b & 0x80000000u) ? b : (b | 0x80000000u);"),
+    "key is the raw bit pattern": ("uint32_t m = (b & 0x80000000u) ? ~b : (b | 0x80000000u);",
+                                   "uint32_t m = b;"),
 }
 
 
@@ -58,13 +63,21 @@ def _bfs_labels(f, t):
     return lab
 
 
+SIGNED = np.array([-0.0, 0.0, -1.5, 2.0, -2.5, 1e-45, -1e-45], np.float32)
+
+
 def _pins_pass() -> bool:
     rng = np.random.default_rng(77)
     for i in range(60):
         shape = tuple(int(x) for x in rng.integers(1, 5, size=3))
-        f = rng.integers(0, 4, size=shape).astype(np.float32) if i % 2 else rng.random(shape, dtype=np.float32)
-        if not np.array_equal(oracle.merge_tree(f), brute_merge_tree(f)):
-            return False
+        if i % 3 == 2:  # signed zeros, negative values and subnormals
+            f = rng.choice(SIGNED, size=shape)
+        else:
+            f = rng.integers(0, 4, size=shape).astype(np.float32) if i % 2 else rng.random(shape, dtype=np.float32)
+        want = brute_merge_tree(f)
+        for method in ("keys", "qsort"):  # both sorts of the sweep
+            if not np.array_equal(oracle.merge_tree(f, method), want):
+                return False
         t = float(f.ravel()[rng.integers(0, f.size)])  # a threshold equal to a value
         if not np.array_equal(oracle.components(f, t), _bfs_labels(f, t)):
             return False
