@@ -85,3 +85,32 @@ def test_batch_oneshot_and_nonfinite():
     with pytest.raises(mt.MtError) as e:
         mt.mt_sync_status(ws)
     assert e.value.code == -3
+
+
+@pytest.mark.slow
+def test_batch_512_config_equals_oracle(tmp_path, monkeypatch):
+    """The batch workload in the configuration the benchmark runs: 512 fields
+    with sides log-uniform in [16, 128] per axis (half white noise, half GRF
+    P(k)~k^-3), autotuned and replayed from a CUDA graph. Every field's
+    triplets and pair list equal the oracle's."""
+    monkeypatch.setenv("MT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    shapes = fields.batch_shapes(512, 16, 128, seed=7)
+    flds = [fields.batch_field(i, s) for i, s in enumerate(shapes)]
+    b = Batch(shapes)
+    b.load(flds)
+    b.tune()
+    b.capture()
+    b.W.zero_()
+    b.launch()
+    torch.cuda.synchronize()
+    mt.mt_sync_status(b.ws)
+    W_all = b.W.cpu().numpy().view(np.uint64)
+    P_all = b.pairs.cpu().numpy().view(np.uint32)
+    npairs = b.npairs.cpu().numpy()
+    for i, f in enumerate(flds):
+        a, e = b.offsets[i], b.offsets[i + 1]
+        W_ref = oracle.merge_tree(f)
+        assert np.array_equal(W_all[a:e], W_ref), f"field {i} {shapes[i]}: triplets differ"
+        p_ref, _ = oracle.pairs(W_ref)
+        assert int(npairs[i]) == len(p_ref), f"field {i}: pair count"
+        assert np.array_equal(P_all[a:a + len(p_ref)], p_ref), f"field {i}: pairs differ"

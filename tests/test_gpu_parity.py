@@ -2,8 +2,7 @@
 
 Triplets, pairs and labels are integers, so the bar is bit-exact equality.
 Sizes run from single vertices to several compaction chunks with ragged
-tails; the 1024^3 workload is checked by structural properties and by
-single-vertex oracle queries (the full oracle would need minutes there).
+tails; the 1024^3 workload is compared in full in test_gpu_full_size.py.
 """
 
 from __future__ import annotations
@@ -16,7 +15,6 @@ import torch
 
 import oracle
 import paper_2301_10838_gb300 as mt
-from checks import check_triplets, local_minima_mask
 from paper_2301_10838_gb300 import fields
 
 pytestmark = pytest.mark.gpu
@@ -204,52 +202,6 @@ def test_bad_arguments_on_device():
     with pytest.raises(mt.MtError) as e:
         mt.mt_build_triplets(f, torch.empty(64, dtype=torch.int64, device="cuda"), ws[1:])
     assert e.value.code == -1
-
-
-@pytest.mark.slow
-def test_full_size_lognormal_1024():
-    """The 1024^3 workload in the configuration the benchmark times:
-    structural properties over every vertex, the local-minima stencil, and
-    single-vertex oracle queries on a sample of vertices and minima."""
-    f = fields.named_field("lognorm1024", seed=1, device="cuda")
-    n = f.numel()
-    W = torch.empty(n, dtype=torch.int64, device="cuda")
-    ws = mt.workspace(mt.grid_of(f))
-    mt.mt_build_triplets(f, W, ws)
-    mt.mt_sync_status(ws)
-    info = check_triplets(f, W)
-    pairs = torch.empty((info["pairs"], 2), dtype=torch.int32, device="cuda")
-    npairs, root = mt.mt_persistence_pairs(f, W, pairs, ws)
-    assert npairs == info["pairs"]
-    del pairs
-    f_np = f.cpu().numpy()
-    W_np = W.cpu().numpy().view(np.uint64)
-    rng = np.random.default_rng(0)
-    flat = f_np.ravel()
-    low = np.nonzero(flat < np.quantile(flat[:: 97], 0.05))[0]
-    sample = np.concatenate([rng.integers(0, n, 200), rng.choice(low, 200)])
-    mins = np.nonzero(local_minima_mask(f).cpu().numpy())[0]
-    sample = np.concatenate([sample, rng.choice(mins, 200)])
-    checked = 0
-    for u in sample:
-        r = oracle.point_triplet(f_np, int(u), budget=1 << 18)
-        if r is not None:
-            checked += 1
-            assert r == int(W_np[u]), f"vertex {u}: oracle {r:#x} gpu {int(W_np[u]):#x}"
-    assert checked >= 200
-    t = float(np.quantile(flat[::101], 0.1))
-    lab = torch.empty(n, dtype=torch.int32, device="cuda")
-    mt.mt_components_at(f, W, t, lab, ws)
-    mt.mt_sync_status(ws)
-    lab_np = lab.cpu().numpy().view(np.uint32)
-    for u in sample[:300]:
-        if flat[u] <= t:
-            # the label is the deepest vertex of u's component of G_t: it lies
-            # at or below t and its own label is itself
-            L = int(lab_np[u])
-            assert flat[L] <= t and int(lab_np[L]) == L
-        else:
-            assert lab_np[u] == 0xFFFFFFFF
 
 
 def test_corrupt_triplets_are_reported_not_followed():
