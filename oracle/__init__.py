@@ -20,6 +20,10 @@ Functions
   simplified_components(f, W, t, eps) -> labels of G_t after filling every
                            branch of persistence < eps up to its saddle
   branches(f, W)           -> (order, offsets): vertices grouped by branch
+  merge_tree_wide(f), pairs_wide(W2), components_wide(f, t),
+  point_triplet_wide(f, u, budget)   the same with 64-bit ids: W2 is
+                           uint64[n, 2] = (s, v), pairs uint64[k, 2], labels
+                           uint64 (all ones outside G_t)
 """
 
 from __future__ import annotations
@@ -73,6 +77,9 @@ def _load():
                 "oracle_pairs": [P, U64, P, U64, P, P, P],
                 "oracle_components": [P, U32, U32, U32, ctypes.c_float, P],
                 "oracle_point_triplet": [P, U32, U32, U32, U64, U64, P],
+                "oracle_merge_tree_wide": [P, U32, U32, U32, P],
+                "oracle_components_wide": [P, U32, U32, U32, ctypes.c_float, P],
+                "oracle_point_triplet_wide": [P, U32, U32, U32, U64, U64, P],
             }.items():
                 fn = getattr(lib, name)
                 fn.argtypes = args
@@ -250,3 +257,44 @@ def branches(f, W: np.ndarray):
     sb = b[order]
     heads = np.nonzero(np.r_[True, sb[1:] != sb[:-1]])[0].astype(np.uint32)
     return order, np.r_[heads, np.uint32(n)].astype(np.uint32)
+
+
+# ---- wide ids (64-bit): the same constructions, for grids of 2^32+ vertices
+
+def merge_tree_wide(f) -> np.ndarray:
+    """Triplets with 64-bit ids: W2[u] = (s, v), uint64 array of shape (n, 2).
+    The sort (qsort on (value, index)) and sweep of merge_tree, widened."""
+    f, nx, ny, nz = _field(f)
+    W2 = np.empty((f.size, 2), dtype=np.uint64)
+    _check(_load().oracle_merge_tree_wide(_ptr(f), nx, ny, nz, _ptr(W2)))
+    return W2
+
+
+def pairs_wide(W2: np.ndarray):
+    """(pairs uint64[k, 2] = (minimum u, saddle s) by ascending u, roots):
+    every u with s != u, and the u with (s, v) = (u, u)."""
+    W2 = np.asarray(W2, dtype=np.uint64).reshape(-1, 2)
+    u = np.arange(W2.shape[0], dtype=np.uint64)
+    m = W2[:, 0] != u
+    pairs = np.stack([u[m], W2[m, 0]], axis=1) if m.any() else np.zeros((0, 2), np.uint64)
+    roots = u[(W2[:, 0] == u) & (W2[:, 1] == u)]
+    return np.ascontiguousarray(pairs, dtype=np.uint64), roots
+
+
+def components_wide(f, t: float) -> np.ndarray:
+    """components() with 64-bit labels (all ones outside G_t)."""
+    f, nx, ny, nz = _field(f)
+    lab = np.empty(f.size, dtype=np.uint64)
+    _check(_load().oracle_components_wide(_ptr(f), nx, ny, nz, ctypes.c_float(t), _ptr(lab)))
+    return lab
+
+
+def point_triplet_wide(f, u: int, budget: int = 1 << 20):
+    """(s, v) of the single vertex u from the definitions, on grids of any
+    size, or None if the query would visit more than ``budget`` vertices."""
+    f, nx, ny, nz = _field(f)
+    out = np.zeros(2, dtype=np.uint64)
+    r = _load().oracle_point_triplet_wide(_ptr(f), nx, ny, nz, int(u), int(budget), _ptr(out))
+    if r < 0:
+        raise OracleError(r)
+    return (int(out[0]), int(out[1])) if r == 1 else None

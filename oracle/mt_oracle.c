@@ -448,13 +448,9 @@ static uint64_t heap_pop(const float *f, uint64_t *h, uint64_t *len)
  * Returns 1 with *Wu set, 0 if the query would visit more than `budget`
  * vertices, or a negative status.
  */
-int oracle_point_triplet(const float *f, uint32_t nx, uint32_t ny, uint32_t nz, uint64_t u, uint64_t budget,
-                         uint64_t *Wu)
+static int point_triplet(const float *f, grid_t g, uint64_t u, uint64_t budget, uint64_t *s_out, uint64_t *v_out)
 {
-    grid_t g;
-    int st = make_grid(nx, ny, nz, &g);
-    if (st) return st;
-    if (!f || !Wu || u >= g.n || budget < 1) return OR_INVALID;
+    if (!f || !s_out || !v_out || u >= g.n || budget < 1) return OR_INVALID;
     if (budget > g.n) budget = g.n;
     idset_t seen;
     if (set_init(&seen, 6 * budget + 8)) return OR_NOMEM;
@@ -471,7 +467,7 @@ int oracle_point_triplet(const float *f, uint32_t nx, uint32_t ny, uint32_t nz, 
     if (has_lower) {
         uint64_t deep;
         ok = bfs_deepest(f, &g, u, u, budget, &seen, buf, &deep);
-        if (ok) *Wu = pack(u, deep);
+        if (ok) *s_out = u, *v_out = deep;
     } else {
         /* priority flood from the minimum u */
         uint64_t len = 0, level = u, popped = 0;
@@ -495,13 +491,186 @@ int oracle_point_triplet(const float *f, uint32_t nx, uint32_t ny, uint32_t nz, 
         if (found) {
             uint64_t deep;
             ok = bfs_deepest(f, &g, u, level, budget, &seen, buf, &deep);
-            if (ok) *Wu = pack(level, deep);
+            if (ok) *s_out = level, *v_out = deep;
         } else if (len == 0 && popped < budget) {
-            *Wu = pack(u, u); /* flood covered the whole grid */
+            *s_out = u, *v_out = u; /* flood covered the whole grid */
             ok = 1;
         }
     }
     free(seen.slot);
     free(buf);
     return ok;
+}
+
+int oracle_point_triplet(const float *f, uint32_t nx, uint32_t ny, uint32_t nz, uint64_t u, uint64_t budget,
+                         uint64_t *Wu)
+{
+    grid_t g;
+    int st = make_grid(nx, ny, nz, &g);
+    if (st) return st;
+    if (!Wu) return OR_INVALID;
+    uint64_t s, v;
+    int r = point_triplet(f, g, u, budget, &s, &v);
+    if (r == 1) *Wu = pack(s, v);
+    return r;
+}
+
+/* ------------------------------------------------------------ wide ids */
+
+/*
+ * The same constructions with 64-bit vertex ids, for grids of 2^32 vertices
+ * and more (Section 3.2 limits the packed pair to 32-bit ids; Section 5
+ * names wider ids as future work). Each triplet is two 64-bit words,
+ * W2[2u] = s and W2[2u + 1] = v. Only the id width differs from the
+ * functions above.
+ */
+static int make_grid_wide(uint32_t nx, uint32_t ny, uint32_t nz, grid_t *g)
+{
+    if (nx == 0 || ny == 0 || nz == 0) return OR_INVALID;
+    g->nx = nx;
+    g->ny = ny;
+    g->nz = nz;
+    g->n = (uint64_t)nx * ny * nz;
+    return OR_OK;
+}
+
+typedef struct {
+    float val;
+    uint64_t idx;
+} keyed_wide_t;
+
+static int cmp_keyed_wide(const void *pa, const void *pb)
+{
+    const keyed_wide_t *a = (const keyed_wide_t *)pa, *b = (const keyed_wide_t *)pb;
+    if (a->val < b->val) return -1;
+    if (a->val > b->val) return 1;
+    if (a->idx < b->idx) return -1;
+    if (a->idx > b->idx) return 1;
+    return 0;
+}
+
+static uint64_t uf_find_wide(uint64_t *parent, uint64_t x)
+{
+    while (parent[x] != x) {
+        parent[x] = parent[parent[x]];
+        x = parent[x];
+    }
+    return x;
+}
+
+/* The sort and sweep of oracle_sort_order / oracle_sweep with 64-bit ids. */
+int oracle_merge_tree_wide(const float *f, uint32_t nx, uint32_t ny, uint32_t nz, uint64_t *W2)
+{
+    grid_t g;
+    int st = make_grid_wide(nx, ny, nz, &g);
+    if (st) return st;
+    if (!f || !W2) return OR_INVALID;
+    st = check_finite(f, g.n);
+    if (st) return st;
+    keyed_wide_t *k = (keyed_wide_t *)malloc(g.n * sizeof(keyed_wide_t));
+    uint64_t *parent = (uint64_t *)malloc(g.n * sizeof(uint64_t));
+    uint64_t *cmin = (uint64_t *)malloc(g.n * sizeof(uint64_t));
+    unsigned char *swept = (unsigned char *)calloc(g.n, 1);
+    if (!k || !parent || !cmin || !swept) {
+        free(k);
+        free(parent);
+        free(cmin);
+        free(swept);
+        return OR_NOMEM;
+    }
+    for (uint64_t i = 0; i < g.n; i++) {
+        k[i].val = f[i];
+        k[i].idx = i;
+    }
+    qsort(k, g.n, sizeof(keyed_wide_t), cmp_keyed_wide);
+    for (uint64_t q = 0; q < g.n; q++) {
+        uint64_t u = k[q].idx;
+        uint64_t nb[6];
+        int nn = neighbours(&g, u, nb);
+        uint64_t roots[6];
+        int nr = 0;
+        for (int j = 0; j < nn; j++) {
+            if (!swept[nb[j]]) continue;
+            uint64_t r = uf_find_wide(parent, nb[j]);
+            int seen = 0;
+            for (int c = 0; c < nr; c++)
+                if (roots[c] == r) seen = 1;
+            if (!seen) roots[nr++] = r;
+        }
+        if (nr == 0) {
+            W2[2 * u] = u;
+            W2[2 * u + 1] = u;
+            parent[u] = u;
+            cmin[u] = u;
+        } else {
+            uint64_t e = roots[0];
+            for (int c = 1; c < nr; c++)
+                if (before(f, cmin[roots[c]], cmin[e])) e = roots[c];
+            W2[2 * u] = u;
+            W2[2 * u + 1] = cmin[e];
+            for (int c = 0; c < nr; c++) {
+                if (roots[c] == e) continue;
+                W2[2 * cmin[roots[c]]] = u;
+                W2[2 * cmin[roots[c]] + 1] = cmin[e];
+                parent[roots[c]] = e;
+            }
+            parent[u] = e;
+        }
+        swept[u] = 1;
+    }
+    free(k);
+    free(parent);
+    free(cmin);
+    free(swept);
+    return OR_OK;
+}
+
+/* oracle_components with 64-bit labels (all ones outside G_t). */
+int oracle_components_wide(const float *f, uint32_t nx, uint32_t ny, uint32_t nz, float t, uint64_t *label)
+{
+    grid_t g;
+    int st = make_grid_wide(nx, ny, nz, &g);
+    if (st) return st;
+    if (!f || !label) return OR_INVALID;
+    st = check_finite(f, g.n);
+    if (st) return st;
+    uint64_t *parent = (uint64_t *)malloc(g.n * sizeof(uint64_t));
+    uint64_t *deep = (uint64_t *)malloc(g.n * sizeof(uint64_t));
+    if (!parent || !deep) {
+        free(parent);
+        free(deep);
+        return OR_NOMEM;
+    }
+    for (uint64_t u = 0; u < g.n; u++) parent[u] = u;
+    for (uint64_t u = 0; u < g.n; u++) {
+        if (!(f[u] <= t)) continue;
+        uint64_t nb[6];
+        int nn = neighbours(&g, u, nb);
+        for (int j = 0; j < nn; j++) {
+            if (!(f[nb[j]] <= t)) continue;
+            uint64_t a = uf_find_wide(parent, u), b = uf_find_wide(parent, nb[j]);
+            if (a != b) parent[a] = b;
+        }
+    }
+    for (uint64_t u = 0; u < g.n; u++) deep[u] = UINT64_MAX;
+    for (uint64_t u = 0; u < g.n; u++) {
+        if (!(f[u] <= t)) continue;
+        uint64_t r = uf_find_wide(parent, u);
+        if (deep[r] == UINT64_MAX || before(f, u, deep[r])) deep[r] = u;
+    }
+    for (uint64_t u = 0; u < g.n; u++) label[u] = (f[u] <= t) ? deep[uf_find_wide(parent, u)] : UINT64_MAX;
+    free(parent);
+    free(deep);
+    return OR_OK;
+}
+
+/* oracle_point_triplet for grids of any size: out[0] = s, out[1] = v. */
+int oracle_point_triplet_wide(const float *f, uint32_t nx, uint32_t ny, uint32_t nz, uint64_t u, uint64_t budget,
+                              uint64_t *out)
+{
+    grid_t g;
+    int st = make_grid_wide(nx, ny, nz, &g);
+    if (st) return st;
+    if (!out) return OR_INVALID;
+    return point_triplet(f, g, u, budget, out, out + 1);
 }

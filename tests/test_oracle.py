@@ -9,6 +9,7 @@ off-diagonal persistence diagram under a change of tie-break.
 
 from __future__ import annotations
 
+import itertools
 import os
 
 import numpy as np
@@ -286,3 +287,107 @@ def test_order_keys_non_finite_refused():
         with pytest.raises(oracle.OracleError) as e:
             oracle.sort_order(f, "keys")
         assert e.value.code == -3
+
+
+def test_wide_oracle_equals_brute_force_and_widened_oracle():
+    """The 64-bit-id oracle (grids of 2^32+ vertices): on tiny grids with
+    ties and signed zeros its triplets are the brute-force tree's, and on
+    larger ones they, its pairs, labels and point queries equal the 32-bit
+    oracle's with the ids widened."""
+    rng = np.random.default_rng(11)
+    for i in range(120):
+        shape = tuple(int(x) for x in rng.integers(1, 5, size=3))
+        f = rng.choice(np.array([-0.0, 0.0, 1.0, 2.0], np.float32), size=shape) if i % 2 else \
+            rng.random(shape, dtype=np.float32)
+        W = brute_merge_tree(f)
+        W2 = oracle.merge_tree_wide(f)
+        assert np.array_equal(W2[:, 0], W >> np.uint64(32)) and np.array_equal(W2[:, 1], W & np.uint64(0xFFFFFFFF))
+    for i in range(30):
+        shape = tuple(int(x) for x in rng.integers(3, 14, size=3))
+        f = rng.integers(0, 6, size=shape).astype(np.float32) if i % 2 else rng.random(shape, dtype=np.float32)
+        W = oracle.merge_tree(f)
+        W2 = oracle.merge_tree_wide(f)
+        assert np.array_equal(W2[:, 0], W >> np.uint64(32)) and np.array_equal(W2[:, 1], W & np.uint64(0xFFFFFFFF))
+        p, r = oracle.pairs(W)
+        p2, r2 = oracle.pairs_wide(W2)
+        assert np.array_equal(p.astype(np.uint64), p2) and np.array_equal(r.astype(np.uint64), r2)
+        t = float(np.median(f))
+        lab = oracle.components(f, t).astype(np.uint64)
+        lab[lab == 0xFFFFFFFF] = np.uint64(0xFFFFFFFFFFFFFFFF)
+        assert np.array_equal(lab, oracle.components_wide(f, t))
+        for u in rng.integers(0, f.size, 5):
+            assert oracle.point_triplet_wide(f, int(u)) == (int(W2[u, 0]), int(W2[u, 1]))
+
+
+def _extrema_1d(g):
+    """Indices of the strict 1-D local minima and maxima of g (an end compares
+    with its one neighbour)."""
+    n = len(g)
+    mins, maxs = set(), set()
+    for i in range(n):
+        lo = all(g[j] > g[i] for j in (i - 1, i + 1) if 0 <= j < n)
+        hi = all(g[j] < g[i] for j in (i - 1, i + 1) if 0 <= j < n)
+        if lo:
+            mins.add(i)
+        if hi:
+            maxs.add(i)
+    return mins, maxs
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sin_product_closed_form(seed):
+    """f = gz(z) gy(y) gx(x), each factor a sampled sine with a phase that
+    keeps every sample away from 0. Along one axis only that axis's factor
+    changes, multiplied by the product p of the other two: where p > 0 the
+    vertex is a minimum along the axis iff its factor is a 1-D minimum, where
+    p < 0 iff its factor is a 1-D maximum. So the local minima are exactly
+    the (z, y, x) whose coordinates each lie in Min or Max of their axis, as
+    the signs of the other two factors decide -- a closed form in the three
+    1-D extrema lists -- and #pairs = #minima - 1. Float32 rounding of the
+    product is monotone in each factor, and no two neighbours tie, so the
+    comparisons of the field are those of the exact products."""
+    rng = np.random.default_rng(100 + seed)
+    sides = [int(x) for x in rng.integers(12, 30, size=3)]
+    gs = []
+    for m in sides:
+        while True:
+            w, ph = rng.uniform(0.3, 1.4), rng.uniform(0, 2 * np.pi)
+            g = np.sin(w * np.arange(m) + ph)
+            if np.abs(g).min() > 1e-2:
+                break
+        gs.append(g)
+    gz, gy, gx = gs
+    f = ((gz[:, None, None] * gy[None, :, None]) * gx[None, None, :]).astype(np.float32)
+    for d in range(3):  # no ties between neighbours
+        assert np.all(np.diff(f, axis=d) != 0)
+    ext = [_extrema_1d(g) for g in gs]
+    sign = [np.sign(g) for g in gs]
+    want = set()
+    for z in range(sides[0]):
+        for y in range(sides[1]):
+            for x in range(sides[2]):
+                c = (z, y, x)
+                ok = True
+                for a in range(3):
+                    p = sign[(a + 1) % 3][c[(a + 1) % 3]] * sign[(a + 2) % 3][c[(a + 2) % 3]]
+                    mins, maxs = ext[a]
+                    ok &= c[a] in (mins if p > 0 else maxs)
+                if ok:
+                    want.add(x + sides[2] * (y + sides[1] * z))
+    # the same count from the 1-D lists alone, sign pattern by sign pattern
+    count = 0
+    for e in itertools.product((1, -1), repeat=3):
+        prod = 1
+        for a in range(3):
+            mins, maxs = ext[a]
+            pick = mins if e[(a + 1) % 3] * e[(a + 2) % 3] > 0 else maxs
+            prod *= sum(1 for i in pick if sign[a][i] == e[a])
+        count += prod
+    assert count == len(want)
+    W = oracle.merge_tree(f)
+    u = np.arange(f.size, dtype=np.uint64)
+    s, v = W >> np.uint64(32), W & np.uint64(0xFFFFFFFF)
+    starts = set(np.nonzero((s != u) | ((s == u) & (v == u)))[0].tolist())
+    assert starts == want
+    p, roots = oracle.pairs(W)
+    assert len(p) == count - 1 and len(roots) == 1

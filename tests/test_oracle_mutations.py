@@ -29,10 +29,16 @@ MUTATIONS = {
                                                          "W[u] = pack(u, cmin[roots[0]]);"),
     "ties broken by the larger index": ("    return a < b;\n}", "    return a > b;\n}"),
     "no +z neighbour": ("    if (z + 1 < g->nz) nb[k++] = u + g->nx * g->ny;\n", ""),
-    "sort breaks ties by the larger index": ("    if (a->idx < b->idx) return -1;\n    if (a->idx > b->idx) return 1;",
-                                             "    if (a->idx < b->idx) return 1;\n    if (a->idx > b->idx) return -1;"),
-    "strict sublevel set": ("        if (!(f[u] <= t)) continue;\n        uint64_t nb[6];",
-                            "        if (!(f[u] < t)) continue;\n        uint64_t nb[6];"),
+    "sort breaks ties by the larger index": (
+        "*b = (const keyed_t *)pb;\n    if (a->val < b->val) return -1;\n    if (a->val > b->val) return 1;\n"
+        "    if (a->idx < b->idx) return -1;\n    if (a->idx > b->idx) return 1;",
+        "*b = (const keyed_t *)pb;\n    if (a->val < b->val) return -1;\n    if (a->val > b->val) return 1;\n"
+        "    if (a->idx < b->idx) return 1;\n    if (a->idx > b->idx) return -1;"),
+    "strict sublevel set": (
+        "        if (!(f[u] <= t)) continue;\n        uint64_t nb[6];\n        int nn = neighbours(&g, u, nb);\n"
+        "        for (int j = 0; j < nn; j++) {\n            if (!(f[nb[j]] <= t)) continue;\n            uint32_t a",
+        "        if (!(f[u] < t)) continue;\n        uint64_t nb[6];\n        int nn = neighbours(&g, u, nb);\n"
+        "        for (int j = 0; j < nn; j++) {\n            if (!(f[nb[j]] <= t)) continue;\n            uint32_t a"),
     "key keeps -0 below +0": ("        if (x == 0.0f) x = 0.0f; /* -0 -> +0 */\n", ""),
     "key of a negative value not flipped": ("uint32_t m = (b & 0x80000000u) ? ~b : (b | 0x80000000u);",
                                            "uint32_t m = (b & 0x80000000u) ? b : (b | 0x80000000u);"),
@@ -203,3 +209,45 @@ def test_numpy_layer_mistake_is_caught(name, attr, fake, pins, monkeypatch):
     monkeypatch.setattr(oracle, attr, fake)
     ok = _simplify_pins_pass() if pins == "simplify" else _branch_pins_pass()
     assert not ok, f"the pins did not catch: {name}"
+
+
+# ---- the 64-bit-id constructions
+
+WIDE_MUTATIONS = {
+    "wide: youngest component survives": ("if (before(f, cmin[roots[c]], cmin[e])) e = roots[c];",
+                                          "if (before(f, cmin[e], cmin[roots[c]])) e = roots[c];"),
+    "wide: dying branch links to the saddle": ("W2[2 * cmin[roots[c]] + 1] = cmin[e];",
+                                               "W2[2 * cmin[roots[c]] + 1] = u;"),
+    "wide: labels keep the first vertex": ("if (deep[r] == UINT64_MAX || before(f, u, deep[r])) deep[r] = u;",
+                                           "if (deep[r] == UINT64_MAX) deep[r] = u;"),
+}
+
+
+def _wide_pins_pass() -> bool:
+    rng = np.random.default_rng(78)
+    for i in range(60):
+        shape = tuple(int(x) for x in rng.integers(1, 5, size=3))
+        f = rng.integers(0, 4, size=shape).astype(np.float32) if i % 2 else rng.random(shape, dtype=np.float32)
+        W = brute_merge_tree(f)
+        W2 = oracle.merge_tree_wide(f)
+        if not (np.array_equal(W2[:, 0], W >> np.uint64(32)) and np.array_equal(W2[:, 1], W & np.uint64(0xFFFFFFFF))):
+            return False
+        t = float(f.ravel()[rng.integers(0, f.size)])
+        lab = _bfs_labels(f, t).astype(np.uint64)
+        lab[lab == 0xFFFFFFFF] = np.uint64(0xFFFFFFFFFFFFFFFF)
+        if not np.array_equal(oracle.components_wide(f, t), lab):
+            return False
+    return True
+
+
+def test_wide_unmodified_source_passes(tmp_path, monkeypatch):
+    _with_source(SOURCE, tmp_path, monkeypatch)
+    assert _wide_pins_pass()
+
+
+@pytest.mark.parametrize("name", sorted(WIDE_MUTATIONS))
+def test_wide_planted_mistake_is_caught(name, tmp_path, monkeypatch):
+    old, new = WIDE_MUTATIONS[name]
+    assert SOURCE.count(old) == 1, name
+    _with_source(SOURCE.replace(old, new), tmp_path, monkeypatch)
+    assert not _wide_pins_pass(), f"the pins did not catch: {name}"

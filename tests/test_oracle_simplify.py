@@ -164,3 +164,38 @@ def test_eps_equal_to_a_persistence_keeps_that_pair():
             assert np.all(lab_r[lab0 == r] == r)
             gr = _filled(f, brute_merge_tree(f), er)
             assert np.array_equal(lab_r != FFFF, gr.ravel() <= np.float32(t))
+
+
+def _cases_large(count, seed, ties):
+    rng = np.random.default_rng(seed)
+    for _ in range(count):
+        shape = tuple(int(x) for x in rng.integers(8, 11, size=3))
+        f = rng.integers(0, 12, size=shape).astype(np.float32) if ties else rng.random(shape, dtype=np.float32)
+        lo, hi = float(f.min()), float(f.max())
+        yield f, float(np.float32(rng.uniform(lo, hi))), float(np.float32(rng.uniform(0.0, (hi - lo) * 0.5)))
+
+
+@pytest.mark.parametrize("ties", [False, True])
+def test_filled_field_pins_on_larger_grids(ties):
+    """The pit-filling pins on grids of 8 to 10 vertices per side (512 to
+    1000 vertices, many nested pits): labels of the simplified G_t, and, on
+    distinct values, the simplified diagram."""
+    for f, t, eps in _cases_large(8, 31 + ties, ties):
+        Wb = brute_merge_tree(f)
+        W = oracle.merge_tree(f)
+        assert np.array_equal(W, Wb)
+        g = _filled(f, Wb, eps)
+        lab = oracle.simplified_components(f, W, t, eps)
+        nz, ny, nx = f.shape
+        nb = _neighbours(nx, ny, nz)
+        keep = g.ravel() <= np.float32(t)
+        assert np.array_equal(lab != FFFF, keep)
+        comp = _components_bfs(keep, nb)
+        flat = [float(x) for x in f.ravel()]
+        for c in range(comp.max() + 1):
+            members = np.nonzero(comp == c)[0]
+            deepest = min(members, key=lambda w: (flat[w], w))
+            assert np.all(lab[members] == deepest)
+        if not ties:
+            pg = oracle.simplified_pairs(g, brute_merge_tree(g), 1e-30)
+            assert np.array_equal(pg, oracle.simplified_pairs(f, W, eps))
