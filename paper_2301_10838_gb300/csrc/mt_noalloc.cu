@@ -11,8 +11,6 @@
 // and stays there until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/mt.h"
 #include "mt_internal.h"
 
@@ -29,27 +27,18 @@ constexpr uint64_t kNoAllocBytes = 512 + (kNoAllocMaxVertices / kCompactChunk) *
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kMaxDevices];
-
-// Device address of the scratch array on the current device. In host code
-// the symbol's name is only a host-side stand-in, so the address is looked up
-// with cudaGetSymbolAddress, once per device, with that device current.
+// Device address of the scratch array in the context current on the calling
+// thread. In host code the symbol's name is only a host-side stand-in, so the
+// address is looked up with cudaGetSymbolAddress. It is looked up on every
+// call rather than cached: an address belongs to one context, and a caller
+// may run in a context other than the device's primary one, or reset the
+// device between calls. The lookup is a host-side query.
 cudaError_t noalloc_scratch(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 }  // namespace

@@ -47,3 +47,36 @@ def test_noalloc_pairs_match_workspace_pairs_twice():
             k, root = mt.mt_persistence_pairs_noalloc(f, W, out)
             assert (k, root) == (k_ref, root_ref)
             assert np.array_equal(out[:k].cpu().numpy(), ref_np)
+
+
+@pytest.mark.gpu
+def test_noalloc_capacity_and_small_after_large():
+    """The capacity path reports the true count, and a small grid right after
+    a large one (whose per-chunk counts are still in the shared array) gets
+    exactly the pairs mt_persistence_pairs gives."""
+    outs = []
+    for shape, seed in (((96, 96, 96), 5), ((9, 11, 13), 6)):
+        f = torch.from_numpy(fields.white_noise(shape, seed)).cuda()
+        n = f.numel()
+        W = torch.empty(n, dtype=torch.int64, device="cuda")
+        ws = mt.workspace(mt.grid_of(f))
+        mt.mt_build_triplets(f, W, ws)
+        ref = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+        k_ref, root_ref = mt.mt_persistence_pairs(f, W, ref, ws)
+        out = torch.full((n, 2), -1, dtype=torch.int32, device="cuda")
+        k, root = mt.mt_persistence_pairs_noalloc(f, W, out)
+        assert (k, root) == (k_ref, root_ref)
+        assert np.array_equal(out[:k].cpu().numpy(), ref[:k_ref].cpu().numpy())
+        outs.append((f, W, ref[:k_ref].cpu().numpy(), k_ref))
+    f, W, ref_np, k_ref = outs[0]
+    cap = 10
+    part = torch.full((cap, 2), -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_persistence_pairs_noalloc(f, W, part)
+    assert e.value.code == -4
+    k, _ = mt.mt_persistence_pairs_noalloc(f, W, part, allow_partial=True)
+    assert k == k_ref
+    assert np.array_equal(part.cpu().numpy(), ref_np[:cap])
+    empty = torch.empty((0, 2), dtype=torch.int32, device="cuda")
+    k, _ = mt.mt_persistence_pairs_noalloc(f, W, empty, allow_partial=True)
+    assert k == k_ref
