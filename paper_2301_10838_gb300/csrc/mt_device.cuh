@@ -52,6 +52,15 @@ __device__ __forceinline__ uint64_t cas_tri(uint64_t *p, uint64_t expect, uint64
 
 __device__ __forceinline__ void raise_status(uint32_t *status, uint32_t bit) { atomicOr(status, bit); }
 
+// Whether a CTA skips its work because an earlier error is recorded. The
+// status word may be raised by another CTA at any moment, so one thread reads
+// it and every thread gets that one answer: kernels with barriers must leave
+// (or stay) as a whole block.
+__device__ __forceinline__ bool block_skips(const uint32_t *status)
+{
+    return __syncthreads_or(threadIdx.x == 0 && *(const volatile uint32_t *)status != 0) != 0;
+}
+
 // The values as the order sees them: f itself (sublevel sets), or -f (sg =
 // -1) for the tree of the superlevel sets, the split tree. Multiplying by -1
 // is exact, and -0 still equals +0.

@@ -44,7 +44,7 @@ template <class Loc, bool SIMP>
 __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32_t *counts, float eps,
                                                                  const uint32_t *status)
 {
-    if (*status) return;
+    if (block_skips(status)) return;
     __shared__ uint32_t warp_sum[kCompactWarps];
     uint64_t local;
     uint32_t fi;
@@ -89,7 +89,7 @@ template <class Loc>
 __global__ void __launch_bounds__(1024) k_scan_counts(Loc loc, uint32_t *counts, uint64_t *npairs,
                                                       const uint32_t *status)
 {
-    if (*status) return;
+    if (block_skips(status)) return;
     __shared__ uint64_t part[1024];
     const FieldDesc fd = loc.field(blockIdx.x);
     uint32_t *cnt = counts + fd.chunk0;
@@ -123,7 +123,7 @@ template <class Loc, bool SIMP>
 __global__ void __launch_bounds__(kCompactThreads) k_pairs_write(Loc loc, const uint32_t *offsets, float eps,
                                                                  const uint32_t *status)
 {
-    if (*status) return;
+    if (block_skips(status)) return;
     __shared__ uint32_t warp_cnt[kCompactWarps];
     uint64_t local;
     uint32_t fi;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kLabThreads, 4) k_labels(const Field f, const 
 {
     const uint32_t n = nx * ny * nz;
     const uint32_t limit = n < kChaseLimit ? n : kChaseLimit;
-    if (*status) return;
+    if (block_skips(status)) return;
     constexpr uint32_t TX = 1u << kLabLX, TY = 1u << kLabLY, TZ = 1u << kLabLZ, TV = TX * TY * TZ;
     constexpr uint32_t HS = 1u << kLabHashLog, NT = kLabThreads, NB = 4;
     constexpr uint32_t EMPTY = 0xFFFFFFFFu, kProbes = 16;
