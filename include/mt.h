@@ -100,6 +100,20 @@ mt_status mt_build_triplets(const float *d_f, mt_grid g, uint64_t *d_W, void *d_
 mt_status mt_build_triplets_ex(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
                                void *stream);
 
+/* mt_build_triplets_ex with a launch configuration cfg (MT_CFG_FOUR_ROUNDS,
+ * MT_CFG_REPAIR_256; MT_CFG_SMALL_TILES is for batches and gives
+ * MT_ERR_INVALID). The triplets do not depend on cfg. */
+mt_status mt_build_triplets_cfg(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
+                                uint32_t cfg, void *stream);
+
+/* Autotuner for single fields: builds the tree of d_f once per
+ * configuration (cfg 0, 2, 4, 6: the single-field knobs) to warm up and three
+ * times timed (CUDA events on `stream`), writes the best times to ms[0..3]
+ * (in that order) and the fastest configuration to *best. d_W receives the
+ * triplets. Synchronises. */
+mt_status mt_build_autotune(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
+                            void *stream, float *ms, uint32_t *best);
+
 /*
  * 0-dimensional persistence pairs of the tree in d_W (Section 1: one point
  * (f(a), f(b)) per branch, a a minimum and b the saddle where it merges).
@@ -216,21 +230,37 @@ size_t mt_batch_workspace_bytes(const mt_grid *h_grids, uint32_t nfields);
 mt_status mt_batch_prepare(const float *d_arena, const mt_grid *h_grids, uint32_t nfields, uint64_t *d_W_arena,
                            uint32_t *d_pairs_arena, void *d_ws, size_t ws_bytes, mt_batch_plan *plan, void *stream);
 
+/* Launch configurations (bits of cfg; 0 is the default). Every
+ * configuration gives the same results; they differ only in speed:
+ *   MT_CFG_SMALL_TILES  16x16x8 tiles of 256 threads instead of 32x16x16 tiles
+ *                       of 1024 threads (batches only: small fields leave
+ *                       most of a large tile empty)
+ *   MT_CFG_FOUR_ROUNDS  4 level buckets per tile instead of 8: the in-tile
+ *                       edges are merged, and their vertices repaired, in 4
+ *                       rounds by level instead of 8 (Algorithm 1 merges the
+ *                       edges in any order)
+ *   MT_CFG_REPAIR_256   the repair kernel (Algorithm 5) in CTAs of 256
+ *                       threads instead of 512 */
+#define MT_CFG_SMALL_TILES 1u
+#define MT_CFG_FOUR_ROUNDS 2u
+#define MT_CFG_REPAIR_256 4u
+#define MT_CFG_COUNT 8
+
 /* Enqueues the batched build and pair compaction on `stream`: memsets and
  * kernel launches only, nothing synchronises, so it may be captured in a
- * CUDA graph. variant 0 uses 32x16x16 tiles, 1 uses 16x16x8 tiles (both give
- * the same results). Device errors land in the workspace status word
- * (mt_sync_status). */
-mt_status mt_batch_launch(const mt_batch_plan *plan, int variant, uint64_t *d_npairs, void *d_ws, size_t ws_bytes,
+ * CUDA graph. cfg is a launch configuration (MT_CFG_* bits, 0 to 7). Device
+ * errors land in the workspace status word (mt_sync_status). */
+mt_status mt_batch_launch(const mt_batch_plan *plan, int cfg, uint64_t *d_npairs, void *d_ws, size_t ws_bytes,
                           void *stream);
 
 /* mt_batch_prepare followed by mt_batch_launch with variant 0. */
 mt_status mt_batch_build(const float *d_arena, const mt_grid *h_grids, uint32_t nfields, uint64_t *d_W_arena,
                          uint32_t *d_pairs_arena, uint64_t *d_npairs, void *d_ws, size_t ws_bytes, void *stream);
 
-/* Autotuner: runs each tile variant once to warm up and three times timed
- * (CUDA events on `stream`), writes the best times to ms[0..1] and the faster
- * variant to *best. Synchronises. */
+/* Autotuner: runs every launch configuration (cfg 0 to MT_CFG_COUNT - 1) of
+ * the batch once to warm up and three times timed (CUDA events on
+ * `stream`), writes the best time of each to ms[0..MT_CFG_COUNT-1] and the
+ * fastest configuration to *best. Synchronises. */
 mt_status mt_batch_autotune(const mt_batch_plan *plan, uint64_t *d_npairs, void *d_ws, size_t ws_bytes, void *stream,
                             float *ms, int *best);
 
@@ -244,6 +274,9 @@ mt_status mt_batch_autotune(const mt_batch_plan *plan, uint64_t *d_npairs, void 
  * field, its persistence pairs and its labels at threshold t, exactly as the
  * single-field calls do; the results do not depend on the other requests.
  * A request needs about 20 bytes of the budget per vertex.
+ * Fairness: a request that has been overtaken by 8 later requests while it
+ * waited for room stops admission behind it until it fits, so a large
+ * request is not starved by a stream of small ones.
  */
 typedef struct mt_server mt_server;
 
@@ -251,6 +284,7 @@ typedef struct {
     mt_status status;  /* MT_OK, or the request's error */
     uint64_t npairs;   /* number of pairs (also when it exceeded pair_cap) */
     uint32_t root;     /* root vertex */
+    uint32_t reused;   /* 1: served from a resident tree (no build), else 0 */
     double t_submit;   /* host steady-clock seconds: submission, */
     double t_admit;    /* admission to a slot, */
     double t_done;     /* results in host memory */
@@ -269,6 +303,28 @@ mt_server *mt_server_create(size_t hbm_budget_bytes, int max_slots, int device);
 mt_status mt_server_submit(mt_server *srv, const float *h_f, mt_grid g, float t, uint32_t *h_pairs,
                            uint64_t pair_cap, uint32_t *h_labels, uint64_t *ticket);
 
+/* Resident fields. A request submitted with a nonzero key keeps its field,
+ * its triplet tree and its pairs on the device after it completes (about 16
+ * bytes of the budget per vertex), under that key. A later request with the
+ * same key reuses them: it computes only the labels at its own threshold and
+ * copies the stored pairs, and its result has reused = 1; h_f may then be
+ * NULL. A key names one field: a request whose grid differs from the resident
+ * one's fails with MT_ERR_INVALID, and a field passed under a key that is
+ * already resident is not read. A request for a key whose build is still
+ * running waits for it. Resident entries that no running request uses are
+ * evicted, least recently used first, when an admission needs their memory;
+ * a request with h_f == NULL whose key is no longer resident fails with
+ * MT_ERR_INVALID. The results equal those of a one-off request. */
+mt_status mt_server_submit_resident(mt_server *srv, uint64_t key, const float *h_f, mt_grid g, float t,
+                                    uint32_t *h_pairs, uint64_t pair_cap, uint32_t *h_labels, uint64_t *ticket);
+
+/* Drops the resident entry of key as soon as no request uses it.
+ * MT_ERR_INVALID if the key is not resident. */
+mt_status mt_server_evict(mt_server *srv, uint64_t key);
+
+/* Number of resident entries that are built, and the device bytes they hold. */
+mt_status mt_server_resident(mt_server *srv, uint64_t *count, uint64_t *bytes);
+
 /* Non-blocking: MT_OK and *r once the request is done (the result is then
  * forgotten), MT_ERR_BUSY while it is pending or running. */
 mt_status mt_server_poll(mt_server *srv, uint64_t ticket, mt_result *r);
@@ -278,6 +334,33 @@ mt_status mt_server_wait(mt_server *srv, uint64_t ticket, mt_result *r);
 
 /* Finishes queued and running requests, then frees the server. */
 void mt_server_destroy(mt_server *srv);
+
+/* ------------------------------------------------------------- wide ids
+ * Grids of 2^32 vertices and more (Section 3.2 caps ids at 32 bits because
+ * SYCL has no double-word compare-and-swap; Section 5 names wider ids as
+ * future work). Each triplet is one 128-bit word of two 64-bit ids,
+ *   W[2u] = s, W[2u + 1] = v      (uint64[n][2], 16-byte aligned),
+ * with the meaning of the 64-bit packing above; it is updated with a 128-bit
+ * compare-and-swap. Ids have 34 bits: 1 <= n < 2^34 (every grid whose field
+ * and triplets fit in one GPU's memory); larger grids get MT_ERR_TOO_LARGE.
+ * The results are those of the 32-bit calls with the ids widened, for any n.
+ * This path runs Algorithm 1 on global memory (no tiles): slower per vertex
+ * than the 32-bit calls.
+ *   flags      0 or MT_SUPERLEVEL, as for mt_build_triplets_ex.
+ *   d_ws       mt_wide_workspace_bytes(g) bytes, 256-byte aligned; status
+ *              word as for the other calls (mt_sync_status reads it).
+ * mt_build_triplets_wide is asynchronous. mt_persistence_pairs_wide writes
+ * (minimum u, saddle s) rows of uint64[cap][2] by ascending u, synchronises
+ * and returns like mt_persistence_pairs (root in *h_root). mt_components_at_wide
+ * writes uint64[n] labels (0xFFFFFFFFFFFFFFFF outside G_t), asynchronously.
+ */
+size_t mt_wide_workspace_bytes(mt_grid g);
+mt_status mt_build_triplets_wide(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes,
+                                 uint32_t flags, void *stream);
+mt_status mt_persistence_pairs_wide(const uint64_t *d_W, mt_grid g, uint64_t *d_pairs, uint64_t cap,
+                                    uint64_t *h_npairs, uint64_t *h_root, void *d_ws, size_t ws_bytes, void *stream);
+mt_status mt_components_at_wide(const float *d_f, const uint64_t *d_W, mt_grid g, float t, uint32_t flags,
+                                uint64_t *d_labels, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
  * Persistence pairs for callers that cannot allocate device memory. The paper
@@ -292,9 +375,12 @@ void mt_server_destroy(mt_server *srv);
  *            process exits. This call allocates and frees nothing.
  *   Limit:   n <= 2^30 vertices (1024^3); larger grids get MT_ERR_TOO_LARGE
  *            before anything is enqueued.
- *   Set-up:  the first call on a device looks up the array's device address
- *            (cudaGetSymbolAddress, with that device current); make that
- *            first call before any stream capture begins.
+ *   Set-up:  every call looks up the array's device address
+ *            (cudaGetSymbolAddress) in the context current on the calling
+ *            thread, so the address always belongs to that context, primary
+ *            or not. The first call on a device may also load libmt's device
+ *            code there: make that first call before any stream capture
+ *            begins.
  *   Sharing: every call uses the same array, which keeps the last call's
  *            contents (each call clears what must start at zero). Calls that
  *            overlap on the GPU (other streams, other host threads) race on it

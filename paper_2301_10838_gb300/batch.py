@@ -1,37 +1,22 @@
 """Batched merge trees over many uneven fields (host-side orchestration).
 
 ``Batch`` packs fields into device arenas, prepares the field table in libmt,
-picks the tile variant with libmt's autotuner (cached per GPU and batch shape
-class in a JSON file), and optionally captures the batched launch in a CUDA
-graph so that a repeated batch costs one graph launch. All merge-tree work
-runs in libmt's kernels.
+picks the launch configuration (tile shape, level buckets, repair CTA size)
+with libmt's autotuner (cached per GPU and batch shape class, ``autotune``),
+and optionally captures the batched launch in a CUDA graph so that a
+repeated batch costs one graph launch. All merge-tree work runs in libmt's
+kernels.
 """
 
 from __future__ import annotations
 
-import json
-import math
-import os
-import threading
-
 import torch
 
+from . import autotune
 from . import binding as B
 
-_CACHE_LOCK = threading.Lock()
-
-
-def _cache_path() -> str:
-    return os.environ.get("MT_AUTOTUNE_CACHE",
-                          os.path.join(os.path.expanduser("~"), ".cache", "mt_gb300_autotune.json"))
-
-
 def shape_class(grids) -> str:
-    """Batch shape class: field count and the log2 of the mean and largest
-    field size (vertices)."""
-    sizes = [g[0] * g[1] * g[2] for g in grids]
-    mean = sum(sizes) / len(sizes)
-    return f"n{len(sizes)}-mean{round(math.log2(mean))}-max{round(math.log2(max(sizes)))}"
+    return autotune.batch_class(grids)
 
 
 class Batch:
@@ -58,7 +43,7 @@ class Batch:
             raise ValueError("invalid batch")
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.plan = B.mt_batch_prepare(self.arena, self.grids, self.W, self.pairs, self.ws)
-        self.variant = 0
+        self.cfg = 0  # launch configuration (MT_CFG_* bits)
         self.graph = None
 
     def field(self, i: int) -> torch.Tensor:
@@ -70,54 +55,39 @@ class Batch:
             self.field(i).copy_(torch.as_tensor(f).reshape(self.shapes[i]), non_blocking=True)
 
     def tune(self, use_cache: bool = True) -> int:
-        """Pick the tile variant: cached result for this GPU and shape class,
-        else libmt's autotuner (which needs the fields loaded)."""
-        key = f"{torch.cuda.get_device_name(self.device)}|{shape_class(self.shapes)}"
-        path = _cache_path()
+        """Pick the launch configuration: cached for this GPU and shape class,
+        else libmt's autotuner over all MT_CFG_COUNT configurations (which
+        needs the fields loaded). Returns it."""
+        cls = autotune.batch_class(self.shapes)
         if use_cache:
-            with _CACHE_LOCK:
-                try:
-                    with open(path) as fh:
-                        cache = json.load(fh)
-                except (OSError, ValueError):
-                    cache = {}
-            if key in cache:
-                self.variant = int(cache[key]["variant"])
-                return self.variant
+            hit = autotune.lookup(self.device, cls)
+            if hit is not None:
+                self.cfg = int(hit["cfg"])
+                return self.cfg
         ms, best = B.mt_batch_autotune(self.plan, self.npairs, self.ws)
-        self.variant = best
+        self.cfg = best
+        self.tuned_ms = ms
         if use_cache:
-            with _CACHE_LOCK:
-                try:
-                    with open(path) as fh:
-                        cache = json.load(fh)
-                except (OSError, ValueError):
-                    cache = {}
-                cache[key] = {"variant": best, "ms": ms}
-                os.makedirs(os.path.dirname(path), exist_ok=True)
-                tmp = path + f".{os.getpid()}"
-                with open(tmp, "w") as fh:
-                    json.dump(cache, fh, indent=1)
-                os.replace(tmp, path)
+            autotune.store(self.device, cls, best, ms)
         return best
 
     def launch(self, stream=None) -> None:
         if self.graph is not None:
             self.graph.replay()
             return
-        B.mt_batch_launch(self.plan, self.variant, self.npairs, self.ws, stream)
+        B.mt_batch_launch(self.plan, self.cfg, self.npairs, self.ws, stream)
 
     def capture(self) -> None:
         """Capture the batched launch in a CUDA graph (tracing must be off)."""
         s = torch.cuda.Stream(self.device)
         s.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.stream(s):
-            B.mt_batch_launch(self.plan, self.variant, self.npairs, self.ws, s)  # warm-up outside the graph
+            B.mt_batch_launch(self.plan, self.cfg, self.npairs, self.ws, s)  # warm-up outside the graph
         torch.cuda.current_stream(self.device).wait_stream(s)
         torch.cuda.synchronize(self.device)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=s):
-            B.mt_batch_launch(self.plan, self.variant, self.npairs, self.ws, s)
+            B.mt_batch_launch(self.plan, self.cfg, self.npairs, self.ws, s)
         self.graph = g
 
     def results(self, i: int):

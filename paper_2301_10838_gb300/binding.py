@@ -35,8 +35,19 @@ __all__ = [
     "mt_sync_status",
     "MT_SUPERLEVEL",
     "mt_build_triplets_ex",
+    "mt_build_triplets_cfg",
+    "mt_build_autotune",
+    "MT_CFG_SMALL_TILES",
+    "MT_CFG_FOUR_ROUNDS",
+    "MT_CFG_REPAIR_256",
+    "MT_CFG_COUNT",
     "mt_components_at_ex",
     "mt_persistence_pairs_noalloc",
+    "mt_wide_workspace_bytes",
+    "wide_workspace",
+    "mt_build_triplets_wide",
+    "mt_persistence_pairs_wide",
+    "mt_components_at_wide",
     "mt_simplified_pairs",
     "mt_simplified_components_at",
     "mt_branches_workspace_bytes",
@@ -51,6 +62,9 @@ __all__ = [
     "MtResult",
     "mt_server_create",
     "mt_server_submit",
+    "mt_server_submit_resident",
+    "mt_server_evict",
+    "mt_server_resident",
     "mt_server_poll",
     "mt_server_wait",
     "mt_server_destroy",
@@ -62,6 +76,11 @@ __all__ = [
 
 MT_OK = 0
 MT_SUPERLEVEL = 1  # flag of the _ex calls: the tree of -f (superlevel sets, the split tree)
+# launch configurations (bits; every one gives the same results)
+MT_CFG_SMALL_TILES = 1  # 16x16x8 tiles of 256 threads (batches only)
+MT_CFG_FOUR_ROUNDS = 2  # 4 level buckets (merge/repair rounds) per tile instead of 8
+MT_CFG_REPAIR_256 = 4   # repair CTAs of 256 threads instead of 512
+MT_CFG_COUNT = 8
 STATUS_NAMES = {0: "MT_OK", -1: "MT_ERR_INVALID", -2: "MT_ERR_TOO_LARGE", -3: "MT_ERR_NONFINITE",
                 -4: "MT_ERR_CAPACITY", -5: "MT_ERR_CUDA", -6: "MT_ERR_NOMEM", -7: "MT_ERR_TIMEOUT",
                 -8: "MT_ERR_BUSY"}
@@ -80,7 +99,8 @@ class Grid(ctypes.Structure):
 
 class MtResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("npairs", ctypes.c_uint64), ("root", ctypes.c_uint32),
-                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+                ("reused", ctypes.c_uint32), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
 
 
 class BatchPlan(ctypes.Structure):
@@ -101,9 +121,17 @@ _SIGS = {
     "mt_components_at": ([_P, _P, Grid, ctypes.c_float, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_sync_status": ([_P, _P], ctypes.c_int32),
     "mt_build_triplets_ex": ([_P, Grid, _P, _P, ctypes.c_size_t, ctypes.c_uint32, _P], ctypes.c_int32),
+    "mt_build_triplets_cfg": ([_P, Grid, _P, _P, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint32, _P],
+                              ctypes.c_int32),
+    "mt_build_autotune": ([_P, Grid, _P, _P, ctypes.c_size_t, ctypes.c_uint32, _P, _P, _P], ctypes.c_int32),
     "mt_components_at_ex": ([_P, _P, Grid, ctypes.c_float, ctypes.c_uint32, _P, _P, ctypes.c_size_t, _P],
                             ctypes.c_int32),
     "mt_persistence_pairs_noalloc": ([_P, _P, Grid, _P, _U64, _P, _P, _P], ctypes.c_int32),
+    "mt_wide_workspace_bytes": ([Grid], ctypes.c_size_t),
+    "mt_build_triplets_wide": ([_P, Grid, _P, _P, ctypes.c_size_t, ctypes.c_uint32, _P], ctypes.c_int32),
+    "mt_persistence_pairs_wide": ([_P, Grid, _P, _U64, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
+    "mt_components_at_wide": ([_P, _P, Grid, ctypes.c_float, ctypes.c_uint32, _P, _P, ctypes.c_size_t, _P],
+                              ctypes.c_int32),
     "mt_simplified_pairs": ([_P, _P, Grid, ctypes.c_float, ctypes.c_uint32, _P, _U64, _P, _P, _P, ctypes.c_size_t, _P],
                             ctypes.c_int32),
     "mt_simplified_components_at": ([_P, _P, Grid, ctypes.c_float, ctypes.c_float, ctypes.c_uint32, _P, _P,
@@ -118,6 +146,9 @@ _SIGS = {
     "mt_batch_autotune": ([_P, _P, _P, ctypes.c_size_t, _P, _P, _P], ctypes.c_int32),
     "mt_server_create": ([ctypes.c_size_t, ctypes.c_int, ctypes.c_int], _P),
     "mt_server_submit": ([_P, _P, Grid, ctypes.c_float, _P, _U64, _P, _P], ctypes.c_int32),
+    "mt_server_submit_resident": ([_P, _U64, _P, Grid, ctypes.c_float, _P, _U64, _P, _P], ctypes.c_int32),
+    "mt_server_evict": ([_P, _U64], ctypes.c_int32),
+    "mt_server_resident": ([_P, _P, _P], ctypes.c_int32),
     "mt_server_poll": ([_P, _U64, _P], ctypes.c_int32),
     "mt_server_wait": ([_P, _U64, _P], ctypes.c_int32),
     "mt_server_destroy": ([_P], None),
@@ -163,14 +194,29 @@ def grid_of(f: torch.Tensor) -> Grid:
 
 
 def _stream_ptr(stream) -> int:
+    """The cudaStream_t of ``stream`` (a torch stream, a raw handle, or None
+    for the current stream). A torch stream must belong to the current
+    device: libmt launches on the current device."""
     if stream is None:
         stream = torch.cuda.current_stream()
-    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    if hasattr(stream, "cuda_stream"):
+        dev = getattr(stream, "device", None)
+        if dev is not None and dev.index is not None and dev.index != torch.cuda.current_device():
+            raise ValueError(f"stream is on {dev}, but the current device is cuda:{torch.cuda.current_device()}")
+        return int(stream.cuda_stream)
+    return int(stream)
 
 
 def _dev(t: torch.Tensor, name: str, dtypes, numel=None) -> int:
+    """Device pointer of ``t`` after checking placement, dtype, layout and
+    size. The tensor must live on the current CUDA device: libmt launches
+    there (and the allocation-free call takes its scratch from it), so a
+    tensor on another GPU would be reached through peer addressing."""
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, but the current device is cuda:{torch.cuda.current_device()}; "
+                         "call under torch.cuda.device(...) of the tensors' device")
     if t.dtype not in dtypes:
         raise ValueError(f"{name} must have dtype in {dtypes}, got {t.dtype}")
     if not t.is_contiguous():
@@ -221,6 +267,30 @@ def mt_build_triplets_ex(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, fla
     _check(load().mt_build_triplets_ex(_dev(f, "f", (torch.float32,)), g, _dev(W, "W", _I64, n),
                                        _dev(ws, "ws", (torch.uint8,)), ws.numel(), int(flags), _stream_ptr(stream)),
            "mt_build_triplets_ex")
+
+
+def mt_build_triplets_cfg(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, flags: int, cfg: int,
+                          stream=None) -> None:
+    """mt_build_triplets_ex with a launch configuration (MT_CFG_FOUR_ROUNDS,
+    MT_CFG_REPAIR_256 bits); the triplets do not depend on it."""
+    g = grid_of(f)
+    n = f.numel()
+    _check(load().mt_build_triplets_cfg(_dev(f, "f", (torch.float32,)), g, _dev(W, "W", _I64, n),
+                                        _dev(ws, "ws", (torch.uint8,)), ws.numel(), int(flags), int(cfg),
+                                        _stream_ptr(stream)), "mt_build_triplets_cfg")
+
+
+def mt_build_autotune(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, flags: int = 0, stream=None):
+    """Times the single-field configurations (cfg 0, 2, 4, 6); returns
+    ({cfg: best ms}, best cfg). W receives the triplets."""
+    g = grid_of(f)
+    n = f.numel()
+    ms = (ctypes.c_float * 4)()
+    best = ctypes.c_uint32(0)
+    _check(load().mt_build_autotune(_dev(f, "f", (torch.float32,)), g, _dev(W, "W", _I64, n),
+                                    _dev(ws, "ws", (torch.uint8,)), ws.numel(), int(flags), _stream_ptr(stream),
+                                    ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(best)), "mt_build_autotune")
+    return {c: float(ms[i]) for i, c in enumerate((0, 2, 4, 6))}, int(best.value)
 
 
 def mt_components_at_ex(f: torch.Tensor, W: torch.Tensor, t: float, flags: int, labels: torch.Tensor,
@@ -347,6 +417,60 @@ def mt_persistence_pairs_noalloc(f: torch.Tensor, W: torch.Tensor, pairs: torch.
     return int(npairs.value), int(root.value)
 
 
+def mt_wide_workspace_bytes(grid: Grid) -> int:
+    return int(load().mt_wide_workspace_bytes(grid))
+
+
+def wide_workspace(grid: Grid, device=None) -> torch.Tensor:
+    """A device byte tensor for the wide-id calls on ``grid``, status cleared."""
+    nbytes = mt_wide_workspace_bytes(grid)
+    if nbytes == 0:
+        raise MtError(-2 if grid.nx and grid.ny and grid.nz else -1, "mt_wide_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+    ws[:768].zero_()
+    return ws
+
+
+def mt_build_triplets_wide(f: torch.Tensor, W2: torch.Tensor, ws: torch.Tensor, flags: int = 0, stream=None) -> None:
+    """Triplets with 64-bit ids: W2 is int64 (n, 2) = (s, v) (uint64 bit
+    patterns), 16-byte aligned. Asynchronous."""
+    g = grid_of(f)
+    n = f.numel()
+    _check(load().mt_build_triplets_wide(_dev(f, "f", (torch.float32,)), g, _dev(W2, "W2", _I64, 2 * n),
+                                         _dev(ws, "ws", (torch.uint8,)), ws.numel(), int(flags), _stream_ptr(stream)),
+           "mt_build_triplets_wide")
+
+
+def mt_persistence_pairs_wide(W2: torch.Tensor, grid: Grid, pairs: torch.Tensor, ws: torch.Tensor, stream=None,
+                              allow_partial: bool = False) -> tuple[int, int]:
+    """(minimum, saddle) rows with 64-bit ids into ``pairs`` (int64 (cap, 2));
+    returns (npairs, root). Synchronises the stream."""
+    n = grid.nx * grid.ny * grid.nz
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must have shape (cap, 2)")
+    cap = int(pairs.shape[0])
+    pp = _dev(pairs, "pairs", _I64) if cap else 0
+    npairs = ctypes.c_uint64(0)
+    root = ctypes.c_uint64(~0 & 0xFFFFFFFFFFFFFFFF)
+    code = load().mt_persistence_pairs_wide(_dev(W2, "W2", _I64, 2 * n), grid, pp, cap, ctypes.byref(npairs),
+                                            ctypes.byref(root), _dev(ws, "ws", (torch.uint8,)), ws.numel(),
+                                            _stream_ptr(stream))
+    if code == -4 and allow_partial:
+        return int(npairs.value), int(root.value)
+    _check(code, "mt_persistence_pairs_wide", f" npairs={npairs.value} cap={cap}")
+    return int(npairs.value), int(root.value)
+
+
+def mt_components_at_wide(f: torch.Tensor, W2: torch.Tensor, t: float, flags: int, labels: torch.Tensor,
+                          ws: torch.Tensor, stream=None) -> None:
+    """64-bit labels (int64[n]; all ones outside G_t). Asynchronous."""
+    g = grid_of(f)
+    n = f.numel()
+    _check(load().mt_components_at_wide(_dev(f, "f", (torch.float32,)), _dev(W2, "W2", _I64, 2 * n), g, float(t),
+                                        int(flags), _dev(labels, "labels", _I64, n), _dev(ws, "ws", (torch.uint8,)),
+                                        ws.numel(), _stream_ptr(stream)), "mt_components_at_wide")
+
+
 def _grid_array(grids):
     arr = (Grid * len(grids))()
     for i, g in enumerate(grids):
@@ -375,10 +499,11 @@ def mt_batch_prepare(arena: torch.Tensor, grids, W_arena: torch.Tensor, pairs_ar
     return plan
 
 
-def mt_batch_launch(plan: BatchPlan, variant: int, npairs: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+def mt_batch_launch(plan: BatchPlan, cfg: int, npairs: torch.Tensor, ws: torch.Tensor, stream=None) -> None:
+    """Enqueues the batched build + pairs with launch configuration cfg."""
     pn = _dev(npairs, "npairs", _I64, plan.nfields)
     pws = _dev(ws, "ws", (torch.uint8,))
-    _check(load().mt_batch_launch(ctypes.byref(plan), int(variant), pn, pws, ws.numel(), _stream_ptr(stream)),
+    _check(load().mt_batch_launch(ctypes.byref(plan), int(cfg), pn, pws, ws.numel(), _stream_ptr(stream)),
            "mt_batch_launch")
 
 
@@ -394,13 +519,14 @@ def mt_batch_build(arena: torch.Tensor, grids, W_arena: torch.Tensor, pairs_aren
 
 
 def mt_batch_autotune(plan: BatchPlan, npairs: torch.Tensor, ws: torch.Tensor, stream=None):
-    """Times both tile variants; returns ([ms0, ms1], best)."""
-    ms = (ctypes.c_float * 2)()
+    """Times every launch configuration of the batch; returns ([ms per cfg],
+    best cfg)."""
+    ms = (ctypes.c_float * MT_CFG_COUNT)()
     best = ctypes.c_int(0)
     _check(load().mt_batch_autotune(ctypes.byref(plan), _dev(npairs, "npairs", _I64, plan.nfields),
                                     _dev(ws, "ws", (torch.uint8,)), ws.numel(), _stream_ptr(stream),
                                     ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(best)), "mt_batch_autotune")
-    return [float(ms[0]), float(ms[1])], int(best.value)
+    return [float(x) for x in ms], int(best.value)
 
 
 def mt_server_create(hbm_budget_bytes: int, max_slots: int, device: int = 0) -> int:
@@ -433,6 +559,33 @@ def mt_server_submit(srv: int, f: torch.Tensor, t: float, pairs: torch.Tensor | 
     ticket = ctypes.c_uint64(0)
     _check(load().mt_server_submit(srv, pf, g, float(t), pp, cap, pl, ctypes.byref(ticket)), "mt_server_submit")
     return int(ticket.value)
+
+
+def mt_server_submit_resident(srv: int, key: int, f: torch.Tensor | None, grid: Grid, t: float,
+                              pairs: torch.Tensor | None, labels: torch.Tensor | None) -> int:
+    """Queues (key, t): builds and keeps the field under ``key`` if it is not
+    resident yet (f, a host float32 tensor, is then required), else reuses
+    the resident tree (f may be None). Returns the ticket."""
+    n = grid.nx * grid.ny * grid.nz
+    pf = _host(f, "f", (torch.float32,), n) if f is not None else 0
+    pp = _host(pairs, "pairs", _I32) if pairs is not None else 0
+    cap = int(pairs.shape[0]) if pairs is not None else 0
+    pl = _host(labels, "labels", _I32, n) if labels is not None else 0
+    ticket = ctypes.c_uint64(0)
+    _check(load().mt_server_submit_resident(srv, int(key), pf, grid, float(t), pp, cap, pl, ctypes.byref(ticket)),
+           "mt_server_submit_resident")
+    return int(ticket.value)
+
+
+def mt_server_evict(srv: int, key: int) -> None:
+    _check(load().mt_server_evict(srv, int(key)), "mt_server_evict")
+
+
+def mt_server_resident(srv: int) -> tuple[int, int]:
+    """(number of built resident entries, device bytes they hold)."""
+    c, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(load().mt_server_resident(srv, ctypes.byref(c), ctypes.byref(b)), "mt_server_resident")
+    return int(c.value), int(b.value)
 
 
 def mt_server_poll(srv: int, ticket: int):

@@ -80,7 +80,7 @@ __global__ void k_readback(const uint64_t *meta, const uint32_t *status, volatil
 }
 
 // out[0..2] = meta (if given), out[3] = status word; synchronises s
-static cudaError_t readback(const uint64_t *meta, const uint32_t *status, cudaStream_t s, uint64_t out[4])
+cudaError_t readback(const uint64_t *meta, const uint32_t *status, cudaStream_t s, uint64_t out[4])
 {
     thread_local uint64_t *h = nullptr, *d = nullptr;
     if (!h) {
@@ -144,6 +144,13 @@ size_t mt_workspace_bytes(mt_grid g)
 mt_status mt_build_triplets_ex(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
                                void *stream)
 {
+    return mt_build_triplets_cfg(d_f, g, d_W, d_ws, ws_bytes, flags, 0u, stream);
+}
+
+mt_status mt_build_triplets_cfg(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
+                                uint32_t cfg, void *stream)
+{
+    if (cfg >= MT_CFG_COUNT || (cfg & MT_CFG_SMALL_TILES)) return MT_ERR_INVALID;
     uint64_t n;
     mt_status st = grid_n(g, n);
     if (st != MT_OK) return st;
@@ -155,9 +162,46 @@ mt_status mt_build_triplets_ex(const float *d_f, mt_grid g, uint64_t *d_W, void 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(ws.status, 0, 256, s) != cudaSuccess) return MT_ERR_CUDA;
     const float sg = (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f;
-    if (launch_build(d_f, d_W, g.nx, g.ny, g.nz, ws, build_faces(d_ws, n), sg, s) != cudaSuccess)
+    if (launch_build(d_f, d_W, g.nx, g.ny, g.nz, ws, build_faces(d_ws, n), sg, s, cfg) != cudaSuccess)
         return MT_ERR_CUDA;
     return MT_OK;
+}
+
+mt_status mt_build_autotune(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
+                            void *stream, float *ms, uint32_t *best)
+{
+    if (!ms || !best) return MT_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess) return MT_ERR_CUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return MT_ERR_CUDA;
+    }
+    static const uint32_t cfgs[4] = {0u, MT_CFG_FOUR_ROUNDS, MT_CFG_REPAIR_256, MT_CFG_FOUR_ROUNDS | MT_CFG_REPAIR_256};
+    mt_status st = MT_OK;
+    for (int i = 0; i < 4 && st == MT_OK; i++) {
+        st = mt_build_triplets_cfg(d_f, g, d_W, d_ws, ws_bytes, flags, cfgs[i], stream);  // warm-up
+        float best_ms = 1e30f;
+        for (int rep = 0; rep < 3 && st == MT_OK; rep++) {
+            cudaEventRecord(a, s);
+            st = mt_build_triplets_cfg(d_f, g, d_W, d_ws, ws_bytes, flags, cfgs[i], stream);
+            cudaEventRecord(b, s);
+            if (cudaEventSynchronize(b) != cudaSuccess) st = MT_ERR_CUDA;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, a, b);
+            if (t < best_ms) best_ms = t;
+        }
+        ms[i] = best_ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != MT_OK) return st;
+    int k = 0;
+    for (int i = 1; i < 4; i++)
+        if (ms[i] < ms[k]) k = i;
+    *best = cfgs[k];
+    return mt_sync_status(d_ws, stream);
 }
 
 mt_status mt_build_triplets(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, void *stream)

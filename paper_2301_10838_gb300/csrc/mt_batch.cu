@@ -135,12 +135,13 @@ mt_status mt_batch_prepare(const float *d_arena, const mt_grid *h_grids, uint32_
     return MT_OK;
 }
 
-mt_status mt_batch_launch(const mt_batch_plan *plan, int variant, uint64_t *d_npairs, void *d_ws, size_t ws_bytes,
+mt_status mt_batch_launch(const mt_batch_plan *plan, int cfg, uint64_t *d_npairs, void *d_ws, size_t ws_bytes,
                           void *stream)
 {
     if (!plan || !d_npairs || !d_ws || ((uintptr_t)d_ws & 255) || ws_bytes < plan->ws_bytes || plan->nfields == 0 ||
-        (variant != 0 && variant != 1) || ((uintptr_t)d_npairs & 7))
+        cfg < 0 || cfg >= MT_CFG_COUNT || ((uintptr_t)d_npairs & 7))
         return MT_ERR_INVALID;
+    const int variant = (cfg & MT_CFG_SMALL_TILES) ? 1 : 0;
     Layout L;
     L.descs[0] = 512;
     L.descs[1] = al256(512 + (size_t)plan->nfields * sizeof(FieldDesc));
@@ -154,7 +155,7 @@ mt_status mt_batch_launch(const mt_batch_plan *plan, int variant, uint64_t *d_np
     if (cudaMemsetAsync(ws + L.meta, 0, (size_t)plan->nfields * 3 * sizeof(uint64_t), s) != cudaSuccess)
         return MT_ERR_CUDA;
     const FieldDesc *descs = reinterpret_cast<const FieldDesc *>(ws + L.descs[variant]);
-    if (launch_batch_build(descs, plan->nfields, plan->tiles[variant], variant, status, queue, s) != cudaSuccess)
+    if (launch_batch_build(descs, plan->nfields, plan->tiles[variant], (uint32_t)cfg, status, queue, s) != cudaSuccess)
         return MT_ERR_CUDA;
     if (launch_batch_pairs(descs, plan->nfields, plan->chunks, reinterpret_cast<uint32_t *>(ws + L.counts), d_npairs,
                            status, s) != cudaSuccess)
@@ -177,27 +178,34 @@ mt_status mt_batch_autotune(const mt_batch_plan *plan, uint64_t *d_npairs, void 
     if (!plan || !ms || !best) return MT_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t a = nullptr, b = nullptr;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return MT_ERR_CUDA;
+    if (cudaEventCreate(&a) != cudaSuccess) return MT_ERR_CUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return MT_ERR_CUDA;
+    }
     mt_status st = MT_OK;
-    for (int v = 0; v < 2 && st == MT_OK; v++) {
-        st = mt_batch_launch(plan, v, d_npairs, d_ws, ws_bytes, stream);  // warm-up
+    for (int c = 0; c < MT_CFG_COUNT && st == MT_OK; c++) {
+        st = mt_batch_launch(plan, c, d_npairs, d_ws, ws_bytes, stream);  // warm-up
         if (st != MT_OK) break;
         float best_ms = 1e30f;
         for (int rep = 0; rep < 3 && st == MT_OK; rep++) {
             cudaEventRecord(a, s);
-            st = mt_batch_launch(plan, v, d_npairs, d_ws, ws_bytes, stream);
+            st = mt_batch_launch(plan, c, d_npairs, d_ws, ws_bytes, stream);
             cudaEventRecord(b, s);
             if (cudaEventSynchronize(b) != cudaSuccess) st = MT_ERR_CUDA;
             float t = 0.f;
             cudaEventElapsedTime(&t, a, b);
             if (t < best_ms) best_ms = t;
         }
-        ms[v] = best_ms;
+        ms[c] = best_ms;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (st != MT_OK) return st;
-    *best = ms[1] < ms[0] ? 1 : 0;
+    int k = 0;
+    for (int c = 1; c < MT_CFG_COUNT; c++)
+        if (ms[c] < ms[k]) k = c;
+    *best = k;
     uint32_t bits = 0;
     if (cudaMemcpy(&bits, d_ws, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess) return MT_ERR_CUDA;
     return status_from_bits(bits);

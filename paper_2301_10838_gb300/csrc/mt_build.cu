@@ -6,6 +6,8 @@
 //   k_repair   Repair (Algorithm 5) via Representative (Algorithm 4)
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mt_device.cuh"
 #include "mt_fields.cuh"
 #include "mt_internal.h"
@@ -592,7 +594,7 @@ constexpr uint32_t kCrossHash = 2048;
 template <int LX, int LY, int LZ, class Loc>
 __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
 {
-    if (*status) return;
+    if (block_skips(status)) return;
     using TS = Tile<LX, LY, LZ>;
     constexpr uint32_t TX = TS::TX, TY = TS::TY, TZ = TS::TZ;
     constexpr uint32_t FX = TY * TZ, FY = TX * TZ, FZ = TX * TY, FH = FX + FY + FZ;
@@ -710,7 +712,7 @@ struct RepairShape {
 template <int LX, int LY, int LZ, int NT, class Loc>
 __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
 {
-    if (*status) return;
+    if (block_skips(status)) return;
     using RS = RepairShape<LX, LY, LZ>;
     constexpr uint32_t TX = 1u << LX, TY = 1u << LY, TV = RS::TV, H = RS::kHops, CAP = RS::kCap,
                        HS = RS::kHash, LIST = RS::kList;
@@ -947,14 +949,14 @@ uint64_t tile_count(int variant, uint32_t nx, uint32_t ny, uint32_t nz)
     return (uint64_t)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * ((nz + tz - 1) / tz);
 }
 
-template <int V, class Loc, bool FULL>
+template <int V, int NB, class Loc, bool FULL>
 static cudaError_t tile_attrs()
 {
     using VV = Variant<V>;
     using TS = Tile<VV::LX, VV::LY, VV::LZ, VV::NT>;
     static bool done = false;  // per instantiation
     if (done) return cudaSuccess;
-    auto ktile = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, Loc, FULL>;
+    auto ktile = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, NB, Loc, FULL>;
     cudaError_t e = cudaFuncSetAttribute(ktile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS::kSmem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(ktile, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -963,39 +965,75 @@ static cudaError_t tile_attrs()
     return cudaSuccess;
 }
 
-template <int V, class Loc>
+template <int V, int NT, class Loc>
 static cudaError_t repair_attrs()
 {
     using VV = Variant<V>;
     static bool done = false;  // per instantiation
     if (done) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(k_repair<VV::LX, VV::LY, VV::LZ, 512, Loc>,
+    const cudaError_t e = cudaFuncSetAttribute(k_repair<VV::LX, VV::LY, VV::LZ, NT, Loc>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)RepairShape<VV::LX, VV::LY, VV::LZ>::kSmem);
     if (e == cudaSuccess) done = true;
     return e;
 }
 
-template <int V, class Loc>
-static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, int persistent_grid, bool full,
-                             uint32_t *status, cudaStream_t st)
+// The tile kernel with NB level buckets (merge rounds); FULL only for a
+// single field whose sides are multiples of the tile's.
+template <int V, int NB, class Loc>
+static cudaError_t launch_tile(const Loc &loc, uint32_t ntiles, uint32_t *queue, int persistent_grid, bool full,
+                               uint32_t *status, cudaStream_t st)
 {
     using VV = Variant<V>;
     using TS = Tile<VV::LX, VV::LY, VV::LZ, VV::NT>;
-    const size_t smem = TS::kSmem;
+    const unsigned grid = queue ? (unsigned)persistent_grid : ntiles;
     cudaError_t e;
-    if ((e = full ? tile_attrs<V, Loc, true>() : tile_attrs<V, Loc, false>()) != cudaSuccess) return e;
+    if constexpr (std::is_same<Loc, OneField>::value) {  // batches never take the FULL form
+        if (full) {
+            if ((e = tile_attrs<V, NB, Loc, true>()) != cudaSuccess) return e;
+            k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, NB, Loc, true><<<grid, VV::NT, TS::kSmem, st>>>(loc, ntiles,
+                                                                                               queue, status);
+            count_launch();
+            return cudaGetLastError();
+        }
+    }
+    {
+        if ((e = tile_attrs<V, NB, Loc, false>()) != cudaSuccess) return e;
+        k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, NB, Loc, false><<<grid, VV::NT, TS::kSmem, st>>>(loc, ntiles, queue,
+                                                                                            status);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int V, int NT, class Loc>
+static cudaError_t launch_repair(const Loc &loc, uint32_t ntiles, uint32_t *status, cudaStream_t st)
+{
+    using VV = Variant<V>;
+    using RS = RepairShape<VV::LX, VV::LY, VV::LZ>;
+    cudaError_t e;
+    if ((e = repair_attrs<V, NT, Loc>()) != cudaSuccess) return e;
+    k_repair<VV::LX, VV::LY, VV::LZ, NT, Loc><<<ntiles, NT, RS::kSmem, st>>>(loc, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Build steps with tile variant V and the knobs of cfg (MT_CFG_* bits of
+// include/mt.h): the number of level buckets of the tile kernel (its merge
+// and repair rounds) and the CTA size of the repair kernel. Every
+// configuration gives the same triplets.
+template <int V, class Loc>
+static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, int persistent_grid, bool full,
+                             uint32_t *status, cudaStream_t st, uint32_t cfg)
+{
+    using VV = Variant<V>;
+    cudaError_t e;
     {
         PhaseScope ps(kTile, st);
-        const unsigned grid = queue ? (unsigned)persistent_grid : ntiles;
-        if (full)
-            k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, Loc, true><<<grid, VV::NT, smem, st>>>(loc, ntiles, queue,
-                                                                                                 status);
-        else
-            k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, Loc, false><<<grid, VV::NT, smem, st>>>(loc, ntiles,
-                                                                                                  queue, status);
-        count_launch();
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = (cfg & MT_CFG_FOUR_ROUNDS)
+                ? launch_tile<V, 4>(loc, ntiles, queue, persistent_grid, full, status, st)
+                : launch_tile<V, kBuckets>(loc, ntiles, queue, persistent_grid, full, status, st);
+        if (e != cudaSuccess) return e;
     }
     {
         PhaseScope ps(kMerge, st);
@@ -1004,15 +1042,12 @@ static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, i
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     PhaseScope ps(kRepair, st);
-    using RS = RepairShape<VV::LX, VV::LY, VV::LZ>;
-    if ((e = repair_attrs<V, Loc>()) != cudaSuccess) return e;
-    k_repair<VV::LX, VV::LY, VV::LZ, 512, Loc><<<ntiles, 512, RS::kSmem, st>>>(loc, status);
-    count_launch();
-    return cudaGetLastError();
+    return (cfg & MT_CFG_REPAIR_256) ? launch_repair<V, 256>(loc, ntiles, status, st)
+                                     : launch_repair<V, 512>(loc, ntiles, status, st);
 }
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         uint32_t *faces, float sg, cudaStream_t st)
+                         uint32_t *faces, float sg, cudaStream_t st, uint32_t cfg)
 {
     using VV = Variant<0>;
     OneField loc;
@@ -1028,20 +1063,21 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
     const uint32_t ntz = (nz + (1u << VV::LZ) - 1) >> VV::LZ;
     const uint64_t ntiles = (uint64_t)loc.d.ntx * loc.d.nty * ntz;
     const bool full = nx % (1u << VV::LX) == 0 && ny % (1u << VV::LY) == 0 && nz % (1u << VV::LZ) == 0;
-    return run_build<0>(loc, (uint32_t)ntiles, nullptr, 0, full, ws.status, st);
+    return run_build<0>(loc, (uint32_t)ntiles, nullptr, 0, full, ws.status, st, cfg);
 }
 
-cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint32_t ntiles, int variant,
+cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint32_t ntiles, uint32_t cfg,
                                uint32_t *status, uint32_t *queue, cudaStream_t st)
 {
     ManyFields loc{d_descs, nfields};
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     // persistent grid: as many CTAs as fit on the GPU at once
-    const int per_sm = variant == 1 ? 1536 / Variant<1>::NT : 2;
+    const bool small = cfg & MT_CFG_SMALL_TILES;
+    const int per_sm = small ? 1536 / Variant<1>::NT : 2;
     const int grid = device_sms() * per_sm;
-    if (variant == 1) return run_build<1>(loc, ntiles, queue, grid, false, status, st);
-    return run_build<0>(loc, ntiles, queue, grid, false, status, st);
+    if (small) return run_build<1>(loc, ntiles, queue, grid, false, status, st, cfg);
+    return run_build<0>(loc, ntiles, queue, grid, false, status, st, cfg);
 }
 
 }  // namespace mt

@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "../../include/mt.h"
+
 namespace mt {
 
 // Vertices per block of the ordered compactions (pairs): 256 threads x 16.
@@ -64,17 +66,21 @@ uint32_t *build_faces(void *base, uint64_t n);
 uint32_t face_words(int variant);
 uint64_t tile_count(int variant, uint32_t nx, uint32_t ny, uint32_t nz);
 int device_sms();
+// Reads meta[0..2] (if meta is given) and the status word into out[0..3]
+// through mapped pinned memory (mt_api.cu); synchronises st.
+cudaError_t readback(const uint64_t *meta, const uint32_t *status, cudaStream_t st, uint64_t out[4]);
+mt_status status_from_bits(uint32_t bits);
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         uint32_t *faces, float sg, cudaStream_t st);
+                         uint32_t *faces, float sg, cudaStream_t st, uint32_t cfg = 0);
 // f, sg, eps: persistence simplification (pairs of persistence below eps
 // dropped; eps <= 0 keeps all and does not read f)
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,
                          cudaStream_t st, const float *f = nullptr, float sg = 1.0f, float eps = 0.0f);
 
 // Batched build and pairs over a packed descriptor table already in device
-// memory; variant selects the tile shape (mt_build.cu, mt_query.cu).
-cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint32_t ntiles, int variant,
+// memory; cfg holds the MT_CFG_* knobs (mt_build.cu, mt_query.cu).
+cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint32_t ntiles, uint32_t cfg,
                                uint32_t *status, uint32_t *queue, cudaStream_t st);
 cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint64_t nchunks, uint32_t *counts,
                                uint64_t *npairs, const uint32_t *status, cudaStream_t st);

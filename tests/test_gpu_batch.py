@@ -1,6 +1,7 @@
 """Batched build: every field of a packed batch gets exactly the triplets
-and pairs the single-field calls give, for both tile variants, one-shot and
-replayed from a CUDA graph."""
+and pairs the single-field calls give, for every launch configuration,
+one-shot and replayed from a CUDA graph; the single-field configurations
+give the oracle's triplets too."""
 
 from __future__ import annotations
 
@@ -32,12 +33,12 @@ def _make(count, seed):
     return shapes, flds
 
 
-@pytest.mark.parametrize("variant", [0, 1])
-def test_batch_matches_single(variant):
+@pytest.mark.parametrize("cfg", range(mt.MT_CFG_COUNT))
+def test_batch_matches_single(cfg):
     shapes, flds = _make(24, 3)
     b = Batch(shapes)
     b.load(flds)
-    b.variant = variant
+    b.cfg = cfg
     b.launch()
     mt.mt_sync_status(b.ws)
     for i, f in enumerate(flds):
@@ -56,7 +57,7 @@ def test_batch_graph_replay_and_autotune(tmp_path, monkeypatch):
     b = Batch(shapes)
     b.load(flds)
     v = b.tune()
-    assert v in (0, 1)
+    assert 0 <= v < mt.MT_CFG_COUNT and len(b.tuned_ms) == mt.MT_CFG_COUNT
     assert b.tune() == v  # now from the cache
     b.capture()
     for rep in range(2):
@@ -114,3 +115,30 @@ def test_batch_512_config_equals_oracle(tmp_path, monkeypatch):
         p_ref, _ = oracle.pairs(W_ref)
         assert int(npairs[i]) == len(p_ref), f"field {i}: pair count"
         assert np.array_equal(P_all[a:a + len(p_ref)], p_ref), f"field {i}: pairs differ"
+
+
+def test_single_field_configurations_equal_oracle(tmp_path, monkeypatch):
+    """mt_build_triplets_cfg: every single-field configuration (level buckets,
+    repair CTA size) gives the oracle's triplets, on a full-tile grid and on
+    ragged ones; the single-field tuner picks one and caches it."""
+    monkeypatch.setenv("MT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    from paper_2301_10838_gb300 import autotune
+
+    for shape, seed in (((32, 32, 64), 1), ((19, 37, 45), 2), ((1, 3, 200), 3)):
+        f_np = fields.grf(shape, -3.0, seed).astype(np.float32) if min(shape) > 1 else \
+            fields.white_noise(shape, seed)
+        f_np = fields.quantize(f_np, 256)
+        W_ref = oracle.merge_tree(f_np)
+        f = torch.from_numpy(f_np).cuda()
+        W = torch.empty(f.numel(), dtype=torch.int64, device="cuda")
+        ws = mt.workspace(mt.grid_of(f))
+        for cfg in (0, mt.MT_CFG_FOUR_ROUNDS, mt.MT_CFG_REPAIR_256, mt.MT_CFG_FOUR_ROUNDS | mt.MT_CFG_REPAIR_256):
+            W.zero_()
+            mt.mt_build_triplets_cfg(f, W, ws, 0, cfg)
+            mt.mt_sync_status(ws)
+            assert np.array_equal(W.cpu().numpy().view(np.uint64), W_ref), (shape, cfg)
+        cfg, ms = autotune.tune_single(f, W, ws)
+        assert cfg in ms and len(ms) == 4
+        assert autotune.tune_single(f, W, ws) == (cfg, None)  # from the cache
+    with pytest.raises(mt.MtError):
+        mt.mt_build_triplets_cfg(f, W, ws, 0, mt.MT_CFG_SMALL_TILES)
