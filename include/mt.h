@@ -344,8 +344,9 @@ void mt_server_destroy(mt_server *srv);
  * compare-and-swap. Ids have 34 bits: 1 <= n < 2^34 (every grid whose field
  * and triplets fit in one GPU's memory); larger grids get MT_ERR_TOO_LARGE.
  * The results are those of the 32-bit calls with the ids widened, for any n.
- * This path runs Algorithm 1 on global memory (no tiles): slower per vertex
- * than the 32-bit calls.
+ * The build runs the tile kernel of mt_build_triplets (16-bit ids inside a
+ * tile), merges the edges between tiles with the 128-bit compare-and-swap and
+ * repairs: about 3x slower per vertex than the 32-bit calls.
  *   flags      0 or MT_SUPERLEVEL, as for mt_build_triplets_ex.
  *   d_ws       mt_wide_workspace_bytes(g) bytes, 256-byte aligned; status
  *              word as for the other calls (mt_sync_status reads it).

@@ -179,9 +179,14 @@ __device__ __forceinline__ void sm_merge(uint32_t *T, const uint32_t *K, uint32_
     ok = false;
 }
 
-template <int LX, int LY, int LZ, int NT, int NB, bool FULL>
+// WIDE: the triplets leave the tile as 128-bit words of two 64-bit ids
+// (W[2u] = s, W[2u + 1] = v) for grids of 2^32 vertices and more; the work
+// inside the tile, on 16-bit local ids, is the same, and no face buffer is
+// written (the wide path merges the edges between tiles from their ends).
+template <int LX, int LY, int LZ, int NT, int NB, bool FULL, bool WIDE = false>
 __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, uint32_t *status)
 {
+    using Id = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
     const float *__restrict__ f = fd.f;
     const float sg = fd.sg;
     uint64_t *__restrict__ W = fd.W;
@@ -214,13 +219,13 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     const uint32_t wx = FULL ? (uint32_t)TX : min((uint32_t)TX, nx - x0),
                    wy = FULL ? (uint32_t)TY : min((uint32_t)TY, ny - y0),
                    wz = FULL ? (uint32_t)TZ : min((uint32_t)TZ, nz - z0);
-    const uint32_t nxy = nx * ny;  // n < 2^32, so every id fits 32 bits
-    const uint32_t base = z0 * nxy + y0 * nx + x0;
+    const Id nxy = (Id)nx * ny;  // n < 2^32 unless WIDE, so every id fits an Id
+    const Id base = (Id)z0 * nxy + (Id)y0 * nx + x0;
     auto lxo = [](uint32_t l) { return l & (TX - 1); };
     auto lyo = [](uint32_t l) { return (l >> LX) & (TY - 1); };
     auto lzo = [](uint32_t l) { return l >> (LX + LY); };
     auto valid = [&](uint32_t l) { return FULL || (lxo(l) < wx && lyo(l) < wy && lzo(l) < wz); };
-    auto gid = [&](uint32_t l) { return base + lzo(l) * nxy + lyo(l) * nx + lxo(l); };
+    auto gid = [&](uint32_t l) -> Id { return base + (Id)lzo(l) * nxy + (Id)lyo(l) * nx + lxo(l); };
     if (threadIdx.x == 0) {
         s_kmin = 0xFFFFFFFFu, s_kmax = 0;
         s_nvalid = wx * wy * wz;
@@ -446,7 +451,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
                 const unsigned long long lev = ((unsigned long long)kS << 32) | S;
                 uint32_t h = (pr * 0x9E3779B1u) >> (32 - HLOG);
                 bool placed = false;
-                for (uint32_t p = 0; p < 16; p++) {
+                for (uint32_t p = 0; p < kTileHashProbes; p++) {
                     uint32_t k0 = vHK[h];
                     if (k0 == 0xFFFFFFFFu) k0 = atomicCAS(hkey + h, 0xFFFFFFFFu, pr);
                     if (k0 == 0xFFFFFFFFu || k0 == pr) {  // the pair's slot: keep the earliest level
@@ -499,7 +504,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     //     id), since the other end lies outside the tile. Face buffer of a
     //     tile: +x, +y, +z, then -x, -y, -z faces, each indexed by the two
     //     in-face coordinates on the full tile extent.
-    if (fd.faces) {
+    if (!WIDE && fd.faces) {
         constexpr uint32_t FX = TY * TZ, FY = TX * TZ, FZ = TX * TY, FH = FX + FY + FZ;
         uint32_t *out = fd.faces + (size_t)tile * (2 * FH);
         const uint32_t has_n = (uint32_t)(x0 + TX < nx) | (uint32_t)(y0 + TY < ny) << 1 |
@@ -532,7 +537,13 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     }
 
     // 7. write the tile's triplets with global ids (coalesced rows)
-    if (vec) {
+    if constexpr (WIDE) {
+        for (uint32_t l = threadIdx.x; l < TV; l += NT) {
+            if (!valid(l)) continue;
+            const uint32_t w = T[l];
+            reinterpret_cast<ulonglong2 *>(W)[gid(l)] = make_ulonglong2(gid(sm_s(w)), gid(sm_v(w)));
+        }
+    } else if (vec) {
         for (uint32_t q = threadIdx.x; q < TV / 2; q += NT) {
             const uint32_t l = 2 * q;
             if (!valid(l)) continue;
@@ -553,14 +564,14 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
 // from a device-side counter until none is left (the batched build). FULL is
 // set when every tile lies inside the grid (grid sides multiples of the tile
 // sides), which drops all partial-tile bounds checks.
-template <int LX, int LY, int LZ, int NT, int NB, class Loc, bool FULL>
+template <int LX, int LY, int LZ, int NT, int NB, class Loc, bool FULL, bool WIDE = false>
 __global__ void __launch_bounds__(NT, NT >= 1024 ? 2 : 1536 / NT) k_tile(Loc loc, uint32_t ntiles, uint32_t *queue,
                                                                       uint32_t *status)
 {
     if (queue == nullptr) {
         uint32_t local;
         const FieldDesc fd = loc.tile(blockIdx.x, local);
-        tile_body<LX, LY, LZ, NT, NB, FULL>(fd, local, status);
+        tile_body<LX, LY, LZ, NT, NB, FULL, WIDE>(fd, local, status);
         return;
     }
     __shared__ uint32_t s_next;
@@ -702,9 +713,9 @@ template <int LX, int LY, int LZ>
 struct RepairShape {
     static constexpr uint32_t TV = 1u << (LX + LY + LZ);
     static constexpr uint32_t kHops = 8;          // links copied per target
-    static constexpr uint32_t kCap = TV / 16;     // copies
-    static constexpr uint32_t kHash = TV / 8;     // hash slots for targets
-    static constexpr uint32_t kList = TV / 4;     // branch minima listed
+    static constexpr uint32_t kCap = TV / 16 / kRepairShrink;   // copies
+    static constexpr uint32_t kHash = TV / 8 / kRepairShrink;   // hash slots for targets
+    static constexpr uint32_t kList = TV / 4 / kRepairShrink;   // branch minima listed
     static constexpr size_t kSmem =
         (size_t)kCap * kHops * 12 + (size_t)kHash * 4 + (size_t)kHash * 2 + (size_t)kList * 2;
 };
@@ -1064,6 +1075,44 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
     const uint64_t ntiles = (uint64_t)loc.d.ntx * loc.d.nty * ntz;
     const bool full = nx % (1u << VV::LX) == 0 && ny % (1u << VV::LY) == 0 && nz % (1u << VV::LZ) == 0;
     return run_build<0>(loc, (uint32_t)ntiles, nullptr, 0, full, ws.status, st, cfg);
+}
+
+// The tile kernel with 64-bit ids and 128-bit output words (the wide path):
+// one CTA per 32x16x16 tile, no face buffer.
+cudaError_t launch_tile_wide(const float *f, uint64_t *W2, uint32_t nx, uint32_t ny, uint32_t nz, float sg,
+                             uint32_t *status, cudaStream_t st)
+{
+    using VV = Variant<0>;
+    using TS = Tile<VV::LX, VV::LY, VV::LZ, VV::NT>;
+    OneField loc;
+    loc.d = FieldDesc{};
+    loc.d.f = f;
+    loc.d.W = W2;
+    loc.d.faces = nullptr;
+    loc.d.sg = sg;
+    loc.d.nx = nx, loc.d.ny = ny, loc.d.nz = nz;
+    loc.d.n = (uint64_t)nx * ny * nz;
+    loc.d.ntx = (nx + (1u << VV::LX) - 1) >> VV::LX;
+    loc.d.nty = (ny + (1u << VV::LY) - 1) >> VV::LY;
+    const uint64_t ntz = (nz + (1u << VV::LZ) - 1) >> VV::LZ;
+    const uint64_t ntiles = (uint64_t)loc.d.ntx * loc.d.nty * ntz;
+    if (ntiles >= 0x80000000ull) return cudaErrorInvalidValue;
+    const bool full = nx % (1u << VV::LX) == 0 && ny % (1u << VV::LY) == 0 && nz % (1u << VV::LZ) == 0;
+    static bool attr[2] = {false, false};
+    auto kfull = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, OneField, true, true>;
+    auto kpart = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, OneField, false, true>;
+    auto kern = full ? kfull : kpart;
+    if (!attr[full]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS::kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr[full] = true;
+    }
+    kern<<<(unsigned)ntiles, VV::NT, TS::kSmem, st>>>(loc, (uint32_t)ntiles, nullptr, status);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint32_t ntiles, uint32_t cfg,

@@ -17,6 +17,21 @@ enum : uint32_t {
     ST_CORRUPT = 8u,  // a triplet array given by the caller holds an id >= n
 };
 
+// Table sizes of the shared-memory hashes and lists. Each table has a path
+// for when it is full (merge in place, repair on the spot, chase the global
+// chain); the defaults keep those paths rare. A library built with
+// MT_STRESS_TABLES shrinks the tables so that the tests reach every such
+// path; its results are the same.
+#ifdef MT_STRESS_TABLES
+constexpr uint32_t kTileHashProbes = 1;   // k_tile: probes before merging in place
+constexpr uint32_t kRepairShrink = 64;    // k_repair: hash, copies and minima list 64x smaller
+constexpr uint32_t kLabelHashLog = 6;     // k_labels: 64 chain starts per brick
+#else
+constexpr uint32_t kTileHashProbes = 16;
+constexpr uint32_t kRepairShrink = 1;
+constexpr uint32_t kLabelHashLog = 12;    // 4096 chain starts per brick
+#endif
+
 // Limits of the bounded device loops. A merge that needs more steps than this
 // gives up and raises ST_TIMEOUT instead of spinning.
 constexpr uint32_t kMergeStepLimit = 1u << 24;

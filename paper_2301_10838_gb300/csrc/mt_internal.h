@@ -80,6 +80,10 @@ cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_
 
 // Batched build and pairs over a packed descriptor table already in device
 // memory; cfg holds the MT_CFG_* knobs (mt_build.cu, mt_query.cu).
+// The tile kernel for the wide-id path: in-tile merge tree of every
+// 32x16x16 tile, written as 128-bit words of two 64-bit ids (mt_build.cu).
+cudaError_t launch_tile_wide(const float *f, uint64_t *W2, uint32_t nx, uint32_t ny, uint32_t nz, float sg,
+                             uint32_t *status, cudaStream_t st);
 cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint32_t ntiles, uint32_t cfg,
                                uint32_t *status, uint32_t *queue, cudaStream_t st);
 cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint64_t nchunks, uint32_t *counts,

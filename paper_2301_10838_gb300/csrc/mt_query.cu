@@ -230,7 +230,7 @@ cudaError_t launch_batch_pairs(const FieldDesc *d_descs, uint32_t nfields, uint6
 // long branch never lies inside a short one's pit.
 constexpr uint32_t kLabLX = 5, kLabLY = 4, kLabLZ = 4;
 constexpr uint32_t kLabThreads = 512;
-constexpr uint32_t kLabHashLog = 12;  // 4096 slots
+constexpr uint32_t kLabHashLog = kLabelHashLog;  // 4096 slots (64 in a stress build)
 constexpr size_t kLabSmem = ((size_t)8 << kLabHashLog) + ((size_t)2 << (kLabLX + kLabLY + kLabLZ));
 
 __global__ void __launch_bounds__(kLabThreads, 4) k_labels(const Field f, const uint64_t *__restrict__ W, uint32_t nx,

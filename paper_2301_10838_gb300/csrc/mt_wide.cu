@@ -5,12 +5,15 @@
 // caps a grid at 2^32 vertices; Section 5 names wider ids as future work. On
 // sm_103a a 128-bit compare-and-swap exists (atom.cas.b128), so this path
 // keeps the whole triplet in one 128-bit word, W[u] = (s, v) with two 64-bit
-// ids, and otherwise runs Algorithm 1 as written: every vertex is seeded with
-// its lowest lower neighbour, every edge is merged with the lock-free Merge
-// (Algorithms 2 and 3) on global memory, and Repair (Algorithms 4 and 5)
-// restores minimality. It computes the same unique triplets as the 32-bit
-// path, only with 64-bit ids; it does not use the tiled shared-memory merges
-// of that path.
+// ids. It computes the same unique triplets as the 32-bit path, in three
+// steps of Algorithm 1 (which merges the edges in any order):
+//   1. the tile kernel of the 32-bit path (mt_build.cu) builds the merge tree
+//      of every 32x16x16 tile in shared memory on 16-bit local ids and writes
+//      it with 64-bit ids (launch_tile_wide);
+//   2. k_w_cross merges every edge between neighbouring tiles with the
+//      lock-free Merge (Algorithms 2 and 3) on the global 128-bit words,
+//      starting from the edge's two ends;
+//   3. k_w_repair restores minimality (Algorithms 4 and 5).
 //
 // Torn reads. While merges run, every 64-bit half of a word carries the same
 // 30-bit version tag above its 34-bit id; a compare-and-swap writes both
@@ -19,17 +22,11 @@
 // climb never follows a pair (s, v) that no Merge wrote, whatever the
 // hardware's atomicity for 128-bit loads. Ids therefore have 34 bits:
 // n < 2^34 vertices, more than fit in the 288 GB of one GB300 at the 20 bytes
-// per vertex the field and the triplets take. Repair writes every word back
-// without its tag.
+// per vertex the field and the triplets take. The tile kernel writes tag 0;
+// repair writes every word back without its tag.
 //
-// Kernels (one thread per vertex or per edge, grid-stride over 64-bit ranges):
-//   k_w_init     validate, seed W[u] = (u, lowest lower neighbour) or (u, u)
-//   k_w_jump     pointer doubling along the descent links (a fixed number of
-//                passes, each a no-op once the previous one changed nothing)
-//   k_w_merge    Merge of every edge whose ends descend to different minima
-//   k_w_repair   Repair, writing the final untagged words
-//   k_w_pairs_count / k_w_scan / k_w_pairs_write   ordered pair compaction
-//   k_w_labels   components at a threshold
+// Pairs and labels: k_w_pairs_count / k_w_scan / k_w_pairs_write (ordered
+// compaction with 64-bit offsets) and k_w_labels (a chase per vertex).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -45,17 +42,14 @@ constexpr uint32_t kIdBits = 34;
 constexpr uint64_t kIdMask = (1ull << kIdBits) - 1;
 constexpr uint64_t kMaxWideVertices = 1ull << kIdBits;
 constexpr uint32_t kTagMask = (1u << (64 - kIdBits)) - 1;
-constexpr int kJumpPasses = kIdBits + 2;  // doubling: chains shorter than 2^34 converge in 34 passes
 constexpr uint32_t kWChunk = 4096;         // vertices per pair-compaction chunk
 constexpr int kWThreads = 256;
 
 // Workspace: [0, 256) status word, [256, 512) meta (npairs, roots, root),
-// [512, 768) jump flags (one u32 per pass), then per-chunk pair counts (u32)
-// and offsets (u64).
+// then per-chunk pair counts (u32) and offsets (u64).
 struct WideWs {
     uint32_t *status;
     uint64_t *meta;
-    uint32_t *jflag;
     uint32_t *counts;
     uint64_t *offsets;
     uint64_t nchunks;
@@ -66,7 +60,7 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t wide_ws_bytes(uint64_t n)
 {
     const uint64_t nchunks = (n + kWChunk - 1) / kWChunk;
-    return 768 + al256(nchunks * 4) + al256(nchunks * 8);
+    return 512 + al256(nchunks * 4) + al256(nchunks * 8);
 }
 
 bool carve(void *base, size_t bytes, uint64_t n, WideWs &ws)
@@ -76,9 +70,8 @@ bool carve(void *base, size_t bytes, uint64_t n, WideWs &ws)
     ws.nchunks = (n + kWChunk - 1) / kWChunk;
     ws.status = reinterpret_cast<uint32_t *>(p);
     ws.meta = reinterpret_cast<uint64_t *>(p + 256);
-    ws.jflag = reinterpret_cast<uint32_t *>(p + 512);
-    ws.counts = reinterpret_cast<uint32_t *>(p + 768);
-    ws.offsets = reinterpret_cast<uint64_t *>(p + 768 + al256(ws.nchunks * 4));
+    ws.counts = reinterpret_cast<uint32_t *>(p + 512);
+    ws.offsets = reinterpret_cast<uint64_t *>(p + 512 + al256(ws.nchunks * 4));
     return true;
 }
 
@@ -98,13 +91,6 @@ __device__ __forceinline__ bool before_w(float fa, uint64_t a, float fb, uint64_
     return fa < fb || (fa == fb && a < b);
 }
 
-__device__ __forceinline__ uint64_t ld_rel(const uint64_t *p)
-{
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // 128-bit compare-and-swap of the word at p (two u64: lo, hi); returns the old word.
 __device__ __forceinline__ void cas128(uint64_t *p, uint64_t cmp_lo, uint64_t cmp_hi, uint64_t new_lo,
                                        uint64_t new_hi, uint64_t &old_lo, uint64_t &old_hi)
@@ -119,85 +105,22 @@ __device__ __forceinline__ void cas128(uint64_t *p, uint64_t cmp_lo, uint64_t cm
                  : "memory");
 }
 
+// Both halves of a word in one 16-byte load (one memory sector); the
+// memory model guarantees each 8-byte half, not the pair.
+__device__ __forceinline__ void ld_word(const uint64_t *W, uint64_t u, uint64_t &lo, uint64_t &hi)
+{
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "l"(W + 2 * u) : "memory");
+}
+
 // A word read during the merges: both halves with the same tag. Returns
 // false if every one of a bounded number of reads was torn.
 __device__ __forceinline__ bool wload(const uint64_t *W, uint64_t u, uint64_t &lo, uint64_t &hi)
 {
     for (int i = 0; i < 1024; i++) {
-        lo = ld_rel(W + 2 * u);
-        hi = ld_rel(W + 2 * u + 1);
+        ld_word(W, u, lo, hi);
         if ((lo >> kIdBits) == (hi >> kIdBits)) return true;
     }
     return false;
-}
-
-__device__ __forceinline__ void wcoords(const Geo &g, uint64_t u, uint64_t &x, uint64_t &y, uint64_t &z)
-{
-    x = u % g.nx;
-    const uint64_t r = u / g.nx;
-    y = r % g.ny;
-    z = r / g.ny;
-}
-
-// ------------------------------------------------------------------ init
-__global__ void __launch_bounds__(kWThreads) k_w_init(FieldW f, Geo g, uint64_t *W, uint32_t *status)
-{
-    bool bad = false;
-    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < g.n; u += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t x, y, z;
-        wcoords(g, u, x, y, z);
-        const float fu = f[u];
-        bad |= !isfinite(fu);
-        uint64_t b = u;
-        float fb = fu;
-        // lowest lower neighbour in the order (value, index)
-        const uint64_t cand[6] = {x > 0 ? u - 1 : u, x + 1 < g.nx ? u + 1 : u, y > 0 ? u - g.nx : u,
-                                  y + 1 < g.ny ? u + g.nx : u, z > 0 ? u - g.nxy : u, z + 1 < g.nz ? u + g.nxy : u};
-#pragma unroll
-        for (int k = 0; k < 6; k++) {
-            const uint64_t w = cand[k];
-            if (w == u) continue;
-            const float fw = f[w];
-            if (before_w(fw, w, fb, b)) b = w, fb = fw;
-        }
-        W[2 * u] = u;      // s = u, tag 0
-        W[2 * u + 1] = b;  // v = lowest lower neighbour, or u
-    }
-    if (bad) raise_status(status, ST_NONFINITE);
-}
-
-// ------------------------------------------------------------------ jump
-// Pass p: every inner vertex u (W[u] = (u, v), v != u) replaces v by the
-// target of v, up to four times; concurrent replacements only move targets
-// further down the same descent path, so any value read is valid. A pass
-// after one that changed nothing returns at once.
-__global__ void __launch_bounds__(kWThreads) k_w_jump(Geo g, uint64_t *W, uint32_t *jflag, int pass,
-                                                      const uint32_t *status)
-{
-    if (__syncthreads_or(threadIdx.x == 0 && (*(const volatile uint32_t *)status != 0 ||
-                                              (pass > 0 && jflag[pass - 1] == 0))))
-        return;
-    bool changed = false;
-    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < g.n; u += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t v0 = ld_rel(W + 2 * u + 1);
-        if (v0 == u) continue;
-        uint64_t v = v0;
-        for (int k = 0; k < 4; k++) {
-            const uint64_t w = ld_rel(W + 2 * v + 1);
-            if (w == v) break;
-            v = w;
-        }
-        if (v != v0) {
-            asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(W + 2 * u + 1), "l"(v) : "memory");
-            changed = true;
-        }
-    }
-    if (__syncthreads_or(changed) && threadIdx.x == 0) atomicOr(jflag + pass, 1u);
-}
-
-__global__ void k_w_jump_check(const uint32_t *jflag, uint32_t *status)
-{
-    if (jflag[kJumpPasses - 1]) raise_status(status, ST_TIMEOUT);
 }
 
 // ----------------------------------------------------------------- merge
@@ -252,45 +175,45 @@ struct WideMerge {
     }
 };
 
-// One thread per (vertex, direction +x/+y/+z). Inner vertices keep their
-// word (u, minimum) through the merges, so the minimum an end descends to is
-// read once; an edge whose ends descend to the same minimum is skipped.
-__global__ void __launch_bounds__(kWThreads) k_w_merge(FieldW f, Geo g, uint64_t *W, uint32_t *status)
+// One CTA per 32x16x16 tile: the edges from the tile to its +x, +y and +z
+// neighbour tiles, each merged from its two ends at the level of its later
+// end (the tile kernel has already merged every edge inside a tile).
+constexpr uint32_t kTX = 32, kTY = 16, kTZ = 16;
+
+__global__ void __launch_bounds__(256) k_w_cross(FieldW f, Geo g, uint32_t ntx, uint32_t nty, uint64_t *W,
+                                                 uint32_t *status)
 {
-    if (*status) return;
+    if (*status) return;  // no barriers below: a per-thread test is enough
+    constexpr uint32_t FX = kTY * kTZ, FY = kTX * kTZ, FZ = kTX * kTY, FH = FX + FY + FZ;
     const WideMerge M{W, f};
+    const uint32_t tile = blockIdx.x;
+    const uint32_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const uint64_t x0 = (uint64_t)tx * kTX, y0 = (uint64_t)ty * kTY, z0 = (uint64_t)tz * kTZ;
+    const uint64_t wx = min((uint64_t)kTX, g.nx - x0), wy = min((uint64_t)kTY, g.ny - y0),
+                   wz = min((uint64_t)kTZ, g.nz - z0);
+    const uint64_t base = z0 * g.nxy + y0 * g.nx + x0;
+    const bool hx = x0 + kTX < g.nx, hy = y0 + kTY < g.ny, hz = z0 + kTZ < g.nz;
     bool ok = true;
-    const uint64_t ne = 3 * g.n;
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < ne; e += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t u = e / 3;
-        const uint32_t d = (uint32_t)(e - 3 * u);
-        uint64_t x, y, z;
-        wcoords(g, u, x, y, z);
-        uint64_t w;
-        if (d == 0) {
-            if (x + 1 >= g.nx) continue;
-            w = u + 1;
-        } else if (d == 1) {
-            if (y + 1 >= g.ny) continue;
-            w = u + g.nx;
+    for (uint32_t e = threadIdx.x; e < FH; e += blockDim.x) {
+        uint64_t a, b;
+        if (e < FX) {
+            const uint64_t ly = e % kTY, lz = e / kTY;
+            if (!hx || ly >= wy || lz >= wz) continue;
+            a = base + lz * g.nxy + ly * g.nx + (kTX - 1);
+            b = a + 1;
+        } else if (e < FX + FY) {
+            const uint64_t k = e - FX, lx = k % kTX, lz = k / kTX;
+            if (!hy || lx >= wx || lz >= wz) continue;
+            a = base + lz * g.nxy + (kTY - 1) * g.nx + lx;
+            b = a + g.nx;
         } else {
-            if (z + 1 >= g.nz) continue;
-            w = u + g.nxy;
+            const uint64_t k = e - FX - FY, lx = k % kTX, ly = k / kTX;
+            if (!hz || lx >= wx || ly >= wy) continue;
+            a = base + (kTZ - 1) * g.nxy + ly * g.nx + lx;
+            b = a + g.nxy;
         }
-        // an inner vertex's word is (x, m) with m its descent minimum; any
-        // other word belongs to a minimum. A minimum's word may be changing:
-        // read it whole (tag-checked), or a torn (old s, new v) would look
-        // like an inner vertex
-        uint64_t ulo, uhi, wlo, whi;
-        if (!wload(W, u, ulo, uhi) || !wload(W, w, wlo, whi)) {
-            ok = false;
-            continue;
-        }
-        const uint64_t mu = (ulo & kIdMask) == u ? (uhi & kIdMask) : u;
-        const uint64_t mw = (wlo & kIdMask) == w ? (whi & kIdMask) : w;
-        if (mu == mw) continue;
-        const uint64_t S = before_w(f[u], u, f[w], w) ? w : u;
-        ok &= M.merge(S, mu, mw);
+        const uint64_t S = before_w(f[a], a, f[b], b) ? b : a;
+        ok &= M.merge(S, a, b);
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
 }
@@ -304,7 +227,9 @@ __device__ __forceinline__ uint64_t w_rep(const uint64_t *W, const FieldW &f, ui
                                           uint32_t &steps)
 {
     for (;;) {
-        const uint64_t s = ld_rel(W + 2 * x) & kIdMask, v = ld_rel(W + 2 * x + 1) & kIdMask;
+        uint64_t lo, hi;
+        ld_word(W, x, lo, hi);
+        const uint64_t s = lo & kIdMask, v = hi & kIdMask;
         if (s == x && v == x) return x;
         if (s != S && !before_w(f[s], s, fS, S)) return x;
         x = v;
@@ -317,7 +242,8 @@ __global__ void __launch_bounds__(kWThreads) k_w_repair(FieldW f, Geo g, uint64_
     if (*status) return;
     bool ok = true;
     for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < g.n; u += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t lo = ld_rel(W + 2 * u), hi = ld_rel(W + 2 * u + 1);
+        uint64_t lo, hi;
+        ld_word(W, u, lo, hi);
         const uint64_t s = lo & kIdMask, v = hi & kIdMask;
         uint64_t r = v;
         if (!(s == u && v == u)) {
@@ -329,10 +255,8 @@ __global__ void __launch_bounds__(kWThreads) k_w_repair(FieldW f, Geo g, uint64_
                 continue;
             }
         }
-        if (r != v || lo != s || hi != v) {
-            asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(W + 2 * u), "l"(s) : "memory");
-            asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(W + 2 * u + 1), "l"(r) : "memory");
-        }
+        if (r != v || lo != s || hi != v)
+            asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(W + 2 * u), "l"(s), "l"(r) : "memory");
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
 }
@@ -435,10 +359,11 @@ __global__ void __launch_bounds__(kWThreads) k_w_labels(FieldW f, uint64_t n, co
             labels[u] = ~0ull;
             continue;
         }
-        const uint64_t su = W[2 * u], vu = W[2 * u + 1];
-        uint64_t x = (su == u && vu != u) ? vu : u;
+        const ulonglong2 wu = reinterpret_cast<const ulonglong2 *>(W)[u];
+        uint64_t x = (wu.x == u && wu.y != u) ? wu.y : u;
         for (uint64_t h = 0;; h++) {
-            const uint64_t s = W[2 * x], v = W[2 * x + 1];
+            const ulonglong2 wx = reinterpret_cast<const ulonglong2 *>(W)[x];
+            const uint64_t s = wx.x, v = wx.y;
             if (s == x && v == x) break;
             if (s >= n || v >= n) {
                 bad = true;
@@ -500,19 +425,17 @@ mt_status mt_build_triplets_wide(const float *d_f, mt_grid g, uint64_t *d_W, voi
     WideWs ws;
     if (!carve(d_ws, ws_bytes, geo.n, ws)) return MT_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const FieldW f{d_f, (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f};
-    if (cudaMemsetAsync(ws.status, 0, 768, s) != cudaSuccess) return MT_ERR_CUDA;
+    const float sg = (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f;
+    const FieldW f{d_f, sg};
+    if (cudaMemsetAsync(ws.status, 0, 512, s) != cudaSuccess) return MT_ERR_CUDA;
     {
         PhaseScope ps(kTile, s);
-        k_w_init<<<grid_for(geo.n), kWThreads, 0, s>>>(f, geo, d_W, ws.status);
-        for (int p = 0; p < kJumpPasses; p++)
-            k_w_jump<<<grid_for(geo.n), kWThreads, 0, s>>>(geo, d_W, ws.jflag, p, ws.status);
-        k_w_jump_check<<<1, 1, 0, s>>>(ws.jflag, ws.status);
-        count_launch(2 + kJumpPasses);
+        if (launch_tile_wide(d_f, d_W, g.nx, g.ny, g.nz, sg, ws.status, s) != cudaSuccess) return MT_ERR_CUDA;
     }
+    const uint32_t ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY, ntz = (g.nz + kTZ - 1) / kTZ;
     {
         PhaseScope ps(kMerge, s);
-        k_w_merge<<<grid_for(3 * geo.n), kWThreads, 0, s>>>(f, geo, d_W, ws.status);
+        k_w_cross<<<ntx * nty * ntz, 256, 0, s>>>(f, geo, ntx, nty, d_W, ws.status);
         count_launch();
     }
     {
