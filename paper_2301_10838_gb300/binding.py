@@ -159,14 +159,17 @@ _SIGS = {
 
 
 def load() -> ctypes.CDLL:
-    """Load libmt.so (built in-tree by ``paper_2301_10838_gb300.build``)."""
+    """Load libmt.so (built in-tree by ``paper_2301_10838_gb300.build``), or
+    the library the MT_LIBRARY environment variable names (another in-tree
+    build of the same sources, such as the tests' stress build)."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(_build.LIB):
-                raise ImportError(f"libmt.so is not built ({_build.LIB}); run "
+            path = os.environ.get("MT_LIBRARY") or _build.LIB
+            if not os.path.exists(path):
+                raise ImportError(f"libmt is not built ({path}); run "
                                   "`python -m paper_2301_10838_gb300.build` on a machine with nvcc")
-            lib = ctypes.CDLL(_build.LIB)
+            lib = ctypes.CDLL(path)
             for name, (args, res) in _SIGS.items():
                 fn = getattr(lib, name)
                 fn.argtypes = args
