@@ -4,9 +4,10 @@
 
 One step is one pass of the whole hot path over the 1024^3 lognormal field
 exp(0.8 g) (g a Gaussian random field with P(k) ~ k^-2, float32, seed 1+rank):
-  mt_build_triplets    (validate, init, descent jumping, merge, repair)
-  mt_persistence_pairs (ordered pair compaction; synchronises)
-  mt_components_at     (labels of G_t at the field's median value)
+  mt_build_triplets_cfg (validate, init, descent jumping, merge, repair; the
+                         launch configuration the autotuner picks)
+  mt_persistence_pairs  (ordered pair compaction; synchronises)
+  mt_components_at      (labels of G_t at the field's median value)
 The field (4 GiB) and triplets (8 GiB) are far larger than the 129 MB L2, so
 no flush is needed between steps. Timing uses CUDA events on the launching
 stream, W untimed warm-up steps, barrier + synchronize on both sides, max over
@@ -48,8 +49,11 @@ def parse():
     ap.add_argument("--side", type=int, default=1024, help="cube side (1024 = the benchmark workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-side", type=int, default=256, help="side of the crop the CPU oracle times")
+    ap.add_argument("--cpu-side", type=int, default=384, help="side of the crop the CPU oracle times")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the split tree, branches and small configs")
+    ap.add_argument("--wide-grid", default="", help="nx,ny,nz: also time the wide-id path on this grid alone")
+    ap.add_argument("--cfg", type=int, default=-1, help="launch configuration to use instead of autotuning")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
@@ -143,9 +147,10 @@ def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 32)) -> dict:
             "labels": 16 * n, "E": E, "E_prime": Ep, "cross_edges": C}
 
 
-def traffic_record(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None if there is none or the kernel source changed since it was taken."""
+def traffic_record(kernel: str) -> dict:
+    """The committed ncu record of `kernel` at the benchmark workload: DRAM
+    bytes per launch and what the profile shows the kernel is limited by.
+    Empty if there is none or the kernel source changed since it was taken."""
     import hashlib
 
     prof = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{WORKLOAD}.json")
@@ -156,8 +161,8 @@ def traffic_record(kernel: str):
         with open(src, "rb") as fh:
             h = hashlib.sha256(fh.read()).hexdigest()[:16]
     except (OSError, ValueError):
-        return None
-    return rec.get("dram_bytes_per_launch") if rec.get("mt_build_cu_sha256_16") == h else None
+        return {}
+    return rec if rec.get("mt_build_cu_sha256_16") == h else {}
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
@@ -226,15 +231,22 @@ def run_ours(args):
     W = torch.empty(n, dtype=torch.int64, device=dev)
     ws = mt.workspace(mt.grid_of(f), device=dev)
     labels = torch.empty(n, dtype=torch.int32, device=dev)
+    # launch configuration: libmt's autotuner for this GPU and shape class
+    from paper_2301_10838_gb300 import autotune
+
+    if args.cfg >= 0:
+        cfg, tune_ms = args.cfg, {}
+    else:
+        cfg, tune_ms = autotune.tune_single(f, W, ws, use_cache=False)
     # pair capacity: the number of local minima minus one, known after one build
-    mt.mt_build_triplets(f, W, ws)
+    mt.mt_build_triplets_cfg(f, W, ws, 0, cfg)
     probe = torch.empty((0, 2), dtype=torch.int32, device=dev)
     npairs, _ = mt.mt_persistence_pairs(f, W, probe, ws, allow_partial=True)
     pairs = torch.empty((npairs, 2), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        mt.mt_build_triplets(f, W, ws)
+        mt.mt_build_triplets_cfg(f, W, ws, 0, cfg)
         np_, root = mt.mt_persistence_pairs(f, W, pairs, ws)
         mt.mt_components_at(f, W, t_thr, labels, ws)
         return np_
@@ -278,7 +290,8 @@ def run_ours(args):
     dom = max((k for k in phases if k in ab), key=lambda k: phases[k][1])
     calls, tot = phases[dom]
     achieved = ab[dom] / (tot / calls / 1e3) / 1e9
-    traffic = traffic_record(dom) if side == 1024 else None
+    prof = traffic_record(dom) if side == 1024 else {}
+    traffic = prof.get("dram_bytes_per_launch")
     step_bytes = sum(ab[k] for k in ("tile", "merge", "repair", "pairs", "labels"))
 
     # end to end through the public API with pinned host buffers: every step
@@ -318,7 +331,7 @@ def run_ours(args):
         def e2e_step(k, last):
             df, dW, dl, dp, dws = bufs[k % depth]
             s_cmp.wait_event(loaded[k % depth])
-            mt.mt_build_triplets(df, dW, dws, stream=s_cmp)
+            mt.mt_build_triplets_cfg(df, dW, dws, 0, cfg, stream=s_cmp)
             mt.mt_components_at(df, dW, t_thr, dl, dws, stream=s_cmp)
             built = torch.cuda.Event()
             built.record(s_cmp)
@@ -352,12 +365,22 @@ def run_ours(args):
                "timing": "host wall clock around K pipelined steps (copies on their own streams), synchronised"}
         del h_f, h_W, h_lab, h_pairs, bufs
 
+    # the split tree (merge tree of -f, the tree the paper's experiments
+    # report) and the branch decomposition on the same 1024^3 field
+    extra = {}
+    if not args.no_extra:
+        extra["split_tree"] = bench_split(f, n, dev)
+        extra["branches"] = bench_branches(f, W, n, dev)
+        extra["wide_ids"] = bench_wide(f, W, t_thr, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(f, args.cpu_side)
     del W, labels, pairs, ws
     f = None
     torch.cuda.empty_cache()
+    if not args.no_extra:
+        extra["configs"] = {name: bench_config(name, dev, peak) for name in ("white64", "grf256q12")}
     batch = None if args.no_batch else bench_batch(args, dev)
     serve = None if args.no_serve else bench_serve(args, dev)
 
@@ -380,7 +403,8 @@ def run_ours(args):
                 "grid": [shape[2], shape[1], shape[0]],
                 "field": "exp(0.8 g), g unit-variance GRF P(k)~k^-2, float32, seed 1+rank",
                 "field_sha256": field_sha,
-                "step": "mt_build_triplets + mt_persistence_pairs + mt_components_at(median)",
+                "step": "mt_build_triplets_cfg(tuned cfg) + mt_persistence_pairs + mt_components_at(median)",
+                "build_cfg": cfg,
                 "threshold": t_thr,
                 "npairs": npairs,
                 "l2": "inputs larger than L2 (4 GiB field, 8 GiB triplets); no flush",
@@ -389,14 +413,24 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "algorithmic_bytes_per_launch": ab[dom],
-                         "ms_per_launch": round(tot / calls, 3)},
+                         "ms_per_launch": round(tot / calls, 3),
+                         # what DRAM actually moved (ncu) over the same live time, and the limiter the
+                         # profile shows: the model bytes above are not what bounds this kernel
+                         "dram_gbs": round(traffic / (tot / calls / 1e3) / 1e9, 1) if traffic else None,
+                         "dram_frac": round(traffic / (tot / calls / 1e3) / 1e9 / peak, 4) if traffic else None,
+                         "limiter": prof.get("limiter"), "profile": prof.get("from")},
             "step_roofline": {"algorithmic_bytes": step_bytes,
                               "frac": round(step_bytes / (ms_step / 1e3) / 1e9 / peak, 4)},
             "phases_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in phases.items()},
+            "autotune": ({"shape_class": autotune.single_class(shape), "chosen_cfg": cfg,
+                          "build_ms_by_cfg": {str(k): round(v, 3) for k, v in tune_ms.items()},
+                          "default_cfg_ms": round(tune_ms[0], 3), "tuned_cfg_ms": round(tune_ms[cfg], 3)}
+                         if tune_ms else {"chosen_cfg": cfg, "tuned": False}),
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "cpu_baseline": cpu,
+            **extra,
             "batch": batch,
             "serve": serve,
         }
@@ -407,11 +441,198 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _events_ms(fn, reps: int, dev, flush=None) -> list[float]:
+    """Device time of fn() per call (CUDA events on the current stream),
+    optionally writing `flush` (a buffer larger than L2) before each call."""
+    import torch
+
+    st = torch.cuda.current_stream(dev)
+    out = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def bench_config(name: str, dev, peak: float) -> dict:
+    """One of the smaller configs (64^3 white noise, 256^3 quantised GRF):
+    the same step as the benchmark (build + pairs + labels at the median),
+    L2 flushed (a 256 MiB write) before each step, median of 9 steps."""
+    import numpy as np
+    import torch
+
+    import paper_2301_10838_gb300 as mt
+    from paper_2301_10838_gb300 import fields
+
+    f = torch.from_numpy(np.ascontiguousarray(fields.named_field(name, seed=1))).to(dev)
+    n = f.numel()
+    W = torch.empty(n, dtype=torch.int64, device=dev)
+    ws = mt.workspace(mt.grid_of(f), device=dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    pairs = torch.empty((n // 2 + 1, 2), dtype=torch.int32, device=dev)
+    t = float(f.reshape(-1).float().median())
+    state = {}
+    from paper_2301_10838_gb300 import autotune
+
+    cfg, tune_ms = autotune.tune_single(f, W, ws, use_cache=False)
+
+    def step():
+        mt.mt_build_triplets_cfg(f, W, ws, 0, cfg)
+        state["k"], _ = mt.mt_persistence_pairs(f, W, pairs, ws)
+        mt.mt_components_at(f, W, t, labels, ws)
+
+    for _ in range(3):
+        step()
+    mt.mt_sync_status(ws)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ms = statistics.median(_events_ms(step, 9, dev, flush))
+    mt.mt_sync_status(ws)
+    ab = algorithmic_bytes(n, tuple(f.shape), state["k"])
+    b = sum(ab[k] for k in ("tile", "merge", "repair", "pairs", "labels"))
+    return {"grid": list(f.shape[::-1]), "mvertices_s": round(n / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 4),
+            "npairs": state["k"], "step_roofline_frac": round(b / (ms / 1e3) / 1e9 / peak, 4),
+            "l2": "flushed (256 MiB write) before every step", "timing": "CUDA events, median of 9 steps",
+            "autotune": {"chosen_cfg": cfg, "build_ms_by_cfg": {str(k): round(v, 4) for k, v in tune_ms.items()}}}
+
+
+def bench_split(f, n: int, dev) -> dict:
+    """The split tree (MT_SUPERLEVEL: the merge tree of -f) + its pairs on
+    the benchmark field, median of 3."""
+    import torch
+
+    import paper_2301_10838_gb300 as mt
+
+    W = torch.empty(n, dtype=torch.int64, device=dev)
+    ws = mt.workspace(mt.grid_of(f), device=dev)
+    probe = torch.empty((0, 2), dtype=torch.int32, device=dev)
+    mt.mt_build_triplets_ex(f, W, ws, mt.MT_SUPERLEVEL)
+    k, _ = mt.mt_persistence_pairs(f, W, probe, ws, allow_partial=True)
+    pairs = torch.empty((k, 2), dtype=torch.int32, device=dev)
+
+    def step():
+        mt.mt_build_triplets_ex(f, W, ws, mt.MT_SUPERLEVEL)
+        mt.mt_persistence_pairs(f, W, pairs, ws)
+
+    step()
+    ms = statistics.median(_events_ms(step, 3, dev))
+    mt.mt_sync_status(ws)
+    return {"mvertices_s": round(n / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 3), "npairs": k,
+            "step": "mt_build_triplets_ex(MT_SUPERLEVEL) + mt_persistence_pairs",
+            "timing": "CUDA events, median of 3 (inputs larger than L2)"}
+
+
+def bench_wide(f, W, t: float, dev, reps: int = 3) -> dict:
+    """The wide-id path (128-bit triplet words, 64-bit ids; Algorithm 1 on
+    global memory, no tiles) on the benchmark field: build + pairs + labels,
+    median of `reps`, and whether its triplets are the 32-bit path's."""
+    import torch
+
+    import paper_2301_10838_gb300 as mt
+
+    n = f.numel()
+    g = mt.grid_of(f)
+    W2 = torch.empty((n, 2), dtype=torch.int64, device=dev)
+    ws = mt.wide_workspace(g, device=dev)
+    lab = torch.empty(n, dtype=torch.int64, device=dev)
+    mt.mt_build_triplets_wide(f, W2, ws)
+    probe = torch.empty((0, 2), dtype=torch.int64, device=dev)
+    k, _ = mt.mt_persistence_pairs_wide(W2, g, probe, ws, allow_partial=True)
+    pairs = torch.empty((k, 2), dtype=torch.int64, device=dev)
+    mt.mt_trace_enable(True)
+    mt.mt_trace_read(reset=True)
+
+    def step():
+        mt.mt_build_triplets_wide(f, W2, ws)
+        mt.mt_persistence_pairs_wide(W2, g, pairs, ws)
+        mt.mt_components_at_wide(f, W2, t, 0, lab, ws)
+
+    ms = statistics.median(_events_ms(step, reps, dev))
+    ph = mt.mt_trace_read(reset=True)
+    mt.mt_trace_enable(False)
+    mt.mt_sync_status(ws)
+    same = bool(torch.equal(W2[:, 0], (W >> 32) & 0xFFFFFFFF) and torch.equal(W2[:, 1], W & 0xFFFFFFFF))
+    return {"mvertices_s": round(n / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 3), "npairs": k,
+            "phases_ms_per_step": {kk: round(v[1] / v[0], 3) for kk, v in ph.items() if v[0]},
+            "equals_32bit_triplets": same,
+            "step": "mt_build_triplets_wide + mt_persistence_pairs_wide + mt_components_at_wide",
+            "timing": f"CUDA events, median of {reps} (inputs larger than L2)"}
+
+
+def bench_wide_grid(spec: str, dev) -> dict:
+    """The wide-id path alone on an nx,ny,nz grid (seeded uniform noise plus a
+    separable low-frequency product of sines, generated on the device)."""
+    import torch
+
+    import paper_2301_10838_gb300 as mt
+
+    nx, ny, nz = (int(v) for v in spec.split(","))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+    ax = [torch.sin(torch.arange(m, device=dev, dtype=torch.float32) * w + p)
+          for m, w, p in ((nz, 0.0213, 0.4), (ny, 0.0187, 1.1), (nx, 0.0241, 2.3))]
+    f = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+    for z0 in range(0, nz, 64):
+        z1 = min(nz, z0 + 64)
+        f[z0:z1] = torch.rand((z1 - z0, ny, nx), generator=gen, device=dev, dtype=torch.float32)
+        f[z0:z1] += 2.0 * ax[0][z0:z1, None, None] * ax[1][None, :, None] * ax[2][None, None, :]
+    n = f.numel()
+    g = mt.grid_of(f)
+    W2 = torch.empty((n, 2), dtype=torch.int64, device=dev)
+    ws = mt.wide_workspace(g, device=dev)
+    mt.mt_trace_enable(True)
+    mt.mt_trace_read(reset=True)
+    ms = _events_ms(lambda: mt.mt_build_triplets_wide(f, W2, ws), 2, dev)
+    ph = mt.mt_trace_read(reset=True)
+    mt.mt_trace_enable(False)
+    mt.mt_sync_status(ws)
+    probe = torch.empty((0, 2), dtype=torch.int64, device=dev)
+    k, root = mt.mt_persistence_pairs_wide(W2, g, probe, ws, allow_partial=True)
+    return {"grid": [nx, ny, nz], "n": n, "build_ms": [round(x, 1) for x in ms], "npairs": k, "root": root,
+            "phases_ms": {kk: round(v[1] / v[0], 2) for kk, v in ph.items() if v[0]},
+            "mvertices_s": round(n / (min(ms) / 1e3) / 1e6, 1)}
+
+
+def bench_branches(f, W, n: int, dev) -> dict:
+    """Branch decomposition of the tree of f (every vertex grouped by branch,
+    each group in vertex order), median of 3."""
+    import torch
+
+    import paper_2301_10838_gb300 as mt
+
+    ws = mt.branches_workspace(mt.grid_of(f), device=dev)
+    order = torch.empty(n, dtype=torch.int32, device=dev)
+    offsets = torch.empty(n // 2 + 2, dtype=torch.int32, device=dev)
+    state = {}
+
+    def step():
+        state["nb"] = mt.mt_branch_decomposition(f, W, 0, order, offsets, ws)
+
+    step()
+    ms = statistics.median(_events_ms(step, 3, dev))
+    del ws
+    return {"mvertices_s": round(n / (ms / 1e3) / 1e6, 1), "ms": round(ms, 3), "branches": state["nb"],
+            "timing": "CUDA events, median of 3 (inputs larger than L2)"}
+
+
+def autotune_class(shapes) -> str:
+    from paper_2301_10838_gb300 import autotune
+
+    return autotune.batch_class(shapes)
+
+
 def bench_batch(args, dev):
     """512 fields of uneven sizes (sides log-uniform in [16, 128] per axis,
     half white noise, half GRF P(k)~k^-3): one CUDA-graph replay of the
-    batched build + pairs against 512 plain per-field calls on one stream,
-    same outputs."""
+    batched build + pairs against 512 plain per-field calls on one stream.
+    Both arms are timed the same way (host wall clock around a synchronised
+    loop of repetitions); outputs are compared field by field (triplets and
+    pair lists)."""
     import numpy as np
     import torch
 
@@ -423,20 +644,20 @@ def bench_batch(args, dev):
     flds = [fields.batch_field(i, s) for i, s in enumerate(shapes)]
     b = Batch(shapes, device=dev)
     b.load(flds)
-    variant = b.tune()
+    cfg = b.tune(use_cache=False)
+    tuned_ms = list(b.tuned_ms)
     b.capture()
     st = torch.cuda.current_stream(dev)
     for _ in range(max(3, args.warmup)):
         b.launch()
     torch.cuda.synchronize(dev)
     reps = max(5, args.steps)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
+    t0 = time.perf_counter()
     for _ in range(reps):
         b.launch()
-    e1.record(st)
     torch.cuda.synchronize(dev)
-    ms_batch = e0.elapsed_time(e1) / reps
+    ms_batch = (time.perf_counter() - t0) * 1e3 / reps
+    ev_batch = statistics.median(_events_ms(b.launch, reps, dev))
     # plain: one field at a time through the single-field calls
     ins, outs = [], []
     for i, s in enumerate(shapes):
@@ -454,33 +675,50 @@ def bench_batch(args, dev):
             ks.append(mt.mt_persistence_pairs(fi, W, P, ws)[0])
         return ks
 
-    plain()
+    for _ in range(2):
+        plain()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    prep = max(2, args.steps // 2)
+    prep = max(3, args.steps // 2)
     for _ in range(prep):
         ks = plain()
     torch.cuda.synchronize(dev)
     ms_plain = (time.perf_counter() - t0) * 1e3 / prep
-    same = all(int(b.npairs[i]) == ks[i] and torch.equal(b.results(i)[0], outs[i][0]) for i in range(len(shapes)))
+    b.launch()
+    torch.cuda.synchronize(dev)
+    same = True
+    for i in range(len(shapes)):
+        Wb, Pb = b.results(i)
+        W, P, _ = outs[i]
+        same &= int(b.npairs[i]) == ks[i] and torch.equal(Wb, W) and torch.equal(Pb, P[:ks[i]])
     nv = sum(int(np.prod(s)) for s in shapes)
-    return {"fields": len(shapes), "vertices": nv, "variant": variant,
+    return {"fields": len(shapes), "vertices": nv, "cfg": cfg,
+            "autotune": {"shape_class": autotune_class(shapes), "ms_by_cfg": [round(x, 3) for x in tuned_ms],
+                         "default_cfg_ms": round(tuned_ms[0], 3), "tuned_cfg_ms": round(tuned_ms[cfg], 3)},
             "fields_per_s_batched": round(len(shapes) / (ms_batch / 1e3), 1),
             "fields_per_s_plain": round(len(shapes) / (ms_plain / 1e3), 1),
-            "ms_per_batch": round(ms_batch, 3), "ms_plain_512": round(ms_plain, 3),
+            "ms_per_batch": round(ms_batch, 3), "ms_per_batch_events": round(ev_batch, 3),
+            "ms_plain_512": round(ms_plain, 3),
             "speedup": round(ms_plain / ms_batch, 2), "identical_outputs": bool(same),
-            "timing": "batched: CUDA-graph replays timed with CUDA events; plain: 512 x (mt_build_triplets + "
-                      "mt_persistence_pairs), host wall clock (each pairs call synchronises)"}
+            "compared": "triplets, pair counts and pair lists of all 512 fields",
+            "timing": "both arms: host wall clock around a synchronised loop of repetitions (batched: graph "
+                      "replays; plain: 512 x (mt_build_triplets + mt_persistence_pairs), each pairs call "
+                      "synchronises as the API does)"}
 
 
 def bench_serve(args, dev):
-    """Poisson request stream (200 req/s) of GRF fields (P(k)~k^-2.5, unit
-    variance, cubic sides log-uniform in [32, 384]), each asking for pairs and
-    labels at a random threshold; p50/p99 latency from submission to results
-    in host memory. A pool of 24 distinct fields is reused cyclically (each
-    request has its own threshold and output buffers). Also: the same request
-    list submitted at once (saturated throughput) against the plain
-    single-field path run back to back on one stream."""
+    """Serving (continuous batching). Every request has its own field: a GRF
+    P(k)~k^-2.5 of unit variance on its own cubic grid (side log-uniform in
+    [32, 384], seed per request), generated on the device before the stream
+    starts and held in pinned host memory, plus its own threshold U(-2, 2);
+    each asks for its pairs and its labels at the threshold. Reported:
+      * the open-loop Poisson stream at 200 req/s: p50/p99 latency from
+        submission to results in host memory, throughput;
+      * the same kind of stream at higher rates, up to saturation;
+      * all requests submitted at once (saturated fields/s) against the plain
+        single-field path run back to back on one stream, outputs compared;
+      * re-queries of resident fields (keyed requests that reuse the tree on
+        the device) against the same queries as one-off requests."""
     import numpy as np
     import torch
 
@@ -489,69 +727,124 @@ def bench_serve(args, dev):
     from paper_2301_10838_gb300.serve import Server
 
     stream = fields.serve_stream(200.0, args.serve_seconds, 32, 384, seed=11)
-    pool_sides = [r.side for r in stream[:24]]
-    pool = []
-    for k, side in enumerate(pool_sides):
-        g = fields.grf((side, side, side), -2.5, 7000 + k, device=str(dev))
-        pool.append(g.cpu().pin_memory())
+    nreq = len(stream)
+    sizes = [r.side ** 3 for r in stream]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    arena = torch.empty(int(offs[-1]), dtype=torch.float32, pin_memory=True)
+    for i, r in enumerate(stream):
+        g = fields.grf((r.side, r.side, r.side), -2.5, r.seed, device=str(dev))
+        arena[int(offs[i]):int(offs[i + 1])].copy_(g.reshape(-1))
         del g
+    torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
-    maxn = max(p.numel() for p in pool)
+    flds = [arena[int(offs[i]):int(offs[i + 1])].view(r.side, r.side, r.side) for i, r in enumerate(stream)]
+    maxn = max(sizes)
     R = 48
     ring = [(torch.empty((maxn // 2 + 1, 2), dtype=torch.int32, pin_memory=True),
              torch.empty(maxn, dtype=torch.int32, pin_memory=True)) for _ in range(R)]
-    srv = Server(hbm_budget_bytes=24 << 30, max_slots=6, device=dev.index or 0)
-    try:
-        # warm-up
-        for k in range(4):
-            P, L = ring[k]
-            srv.wait(srv.submit(pool[k], 0.0, pairs=P, labels=L))
-        # open-loop Poisson arrivals
-        import threading
+    slots = 6
+    srv = Server(hbm_budget_bytes=24 << 30, max_slots=slots, device=dev.index or 0)
 
-        results = [None] * len(stream)
-        tickets = [None] * len(stream)
+    def open_loop(rate, count, seed):
+        """count requests (fields 0..count-1) with Poisson arrivals at rate."""
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        tickets = [None] * count
         t_start = time.perf_counter()
 
         def submitter():
-            for i, r in enumerate(stream):
-                delay = t_start + r.arrival_s - time.perf_counter()
+            for i in range(count):
+                delay = t_start + arrivals[i] - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
                 P, L = ring[i % R]
-                tickets[i] = srv.submit(pool[i % len(pool)], r.threshold, pairs=P, labels=L)
+                tickets[i] = srv.submit(flds[i], stream[i].threshold, pairs=P, labels=L)
 
         th = threading.Thread(target=submitter)
         th.start()
-        for i in range(len(stream)):
+        res = []
+        for i in range(count):
             while tickets[i] is None:
                 time.sleep(0.0002)
-            results[i] = srv.wait(tickets[i])
+            res.append(srv.wait(tickets[i]))
         th.join()
         wall = time.perf_counter() - t_start
-        lat = np.array([r["latency_s"] for r in results]) * 1e3
-        nvert = sum(pool[i % len(pool)].numel() for i in range(len(stream)))
-        # saturated: every request of the list submitted at once
-        nsat = min(len(stream), 240)
+        lat = np.array([r["latency_s"] for r in res]) * 1e3
+        queue = np.array([r["queue_s"] for r in res]) * 1e3
+        nv = sum(sizes[:count])
+        slow = np.argsort(-lat)[:5]
+        t0 = min(r["t_submit"] for r in res)
+        return {"rate_hz": rate, "requests": count, "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "p99_queue_ms": round(float(np.percentile(queue, 99)), 3),
+                "p99_service_ms": round(float(np.percentile(lat - queue, 99)), 3),
+                "slowest": [{"side": stream[i].side, "at_s": round(res[i]["t_submit"] - t0, 3),
+                             "queue_ms": round(float(queue[i]), 2), "service_ms": round(float(lat[i] - queue[i]), 2)}
+                            for i in slow],
+                "throughput_req_s": round(count / wall, 1), "mvertices_s": round(nv / wall / 1e6, 1)}
+
+    try:
+        for k in range(4):  # warm-up
+            P, L = ring[k]
+            srv.wait(srv.submit(flds[k], 0.0, pairs=P, labels=L))
+        main = open_loop(200.0, nreq, 11)
+        sweep = [open_loop(rate, min(nreq, cnt), 20 + j)
+                 for j, (rate, cnt) in enumerate(((500.0, 600), (1000.0, 600), (2000.0, 600)))]
+        # saturated: every request of a list submitted at once
+        nsat = min(nreq, 240)
         t0 = time.perf_counter()
         tks = []
         for i in range(nsat):
             P, L = ring[i % R]
-            tks.append(srv.submit(pool[i % len(pool)], stream[i].threshold, pairs=P, labels=L))
+            tks.append(srv.submit(flds[i], stream[i].threshold, pairs=P, labels=L))
             if len(tks) > R - 8:  # keep ring buffers unshared
                 srv.wait(tks.pop(0))
         for tk in tks:
             srv.wait(tk)
         sat = nsat / (time.perf_counter() - t0)
+        # served outputs of the first requests, kept for the comparison below
+        ncmp = 16
+        served = []
+        for i in range(ncmp):
+            o = srv.wait(srv.submit(flds[i], stream[i].threshold))
+            served.append((o["npairs"], o["pairs"].clone(), o["labels"].clone()))
+        # resident fields: 20 fields, 200 queries at random thresholds, as
+        # keyed re-queries (tree kept on the device) and as one-off requests
+        rng = np.random.default_rng(5)
+        keys = list(range(20))
+        for k in keys:
+            srv.wait(srv.submit_resident(1000 + k, flds[k], 0.0))
+        qs = [(int(rng.integers(0, 20)), float(rng.uniform(-2, 2))) for _ in range(200)]
+
+        def run_queries(resident):
+            t0 = time.perf_counter()
+            tks = []
+            for j, (k, t) in enumerate(qs):
+                P, L = ring[j % R]
+                if resident:
+                    tks.append(srv.submit_resident(1000 + k, None, t, shape=tuple(flds[k].shape), pairs=P, labels=L))
+                else:
+                    tks.append(srv.submit(flds[k], t, pairs=P, labels=L))
+                if len(tks) > R - 8:
+                    srv.wait(tks.pop(0))
+            outs = [srv.wait(tk) for tk in tks]
+            return len(qs) / (time.perf_counter() - t0), outs
+
+        res_rate, res_outs = run_queries(True)
+        one_rate, _ = run_queries(False)
+        resident = {"fields": len(keys), "queries": len(qs),
+                    "queries_per_s_resident": round(res_rate, 1), "queries_per_s_one_off": round(one_rate, 1),
+                    "speedup": round(res_rate / one_rate, 2),
+                    "reused": all(o["reused"] for o in res_outs)}
     finally:
         srv.close()
     # plain single-field path, back to back on one stream, same work
     ws_cache = {}
+    plain_out = []
+    nplain = min(nreq, 120)
     t0 = time.perf_counter()
-    nplain = min(len(stream), 120)
     for i in range(nplain):
-        h = pool[i % len(pool)]
-        fd = h.to(dev, non_blocking=True)
+        fd = flds[i].to(dev, non_blocking=True)
         n = fd.numel()
         if n not in ws_cache:
             ws_cache[n] = (torch.empty(n, dtype=torch.int64, device=dev),
@@ -564,33 +857,79 @@ def bench_serve(args, dev):
         P, L = ring[i % R]
         P[:k].copy_(Pd[:k])
         L[:n].copy_(Ld)
+        if i < ncmp:
+            torch.cuda.synchronize(dev)
+            plain_out.append((k, P[:k].clone(), L[:n].clone()))
     torch.cuda.synchronize(dev)
     plain = nplain / (time.perf_counter() - t0)
-    return {"requests": len(stream), "rate_hz": 200.0, "seconds": args.serve_seconds,
-            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "throughput_req_s": round(len(stream) / wall, 1),
-            "mvertices_s_offered": round(nvert / wall / 1e6, 1),
+    same = all(a[0] == b[0] and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+               for a, b in zip(served, plain_out))
+    del arena, flds
+    return {"requests": nreq, "rate_hz": 200.0, "seconds": args.serve_seconds,
+            "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "p99_queue_ms": main["p99_queue_ms"],
+            "p99_service_ms": main["p99_service_ms"], "slowest": main["slowest"],
+            "throughput_req_s": main["throughput_req_s"], "mvertices_s_offered": main["mvertices_s"],
+            "rate_sweep": sweep,
             "saturated_fields_per_s": round(sat, 1), "plain_fields_per_s": round(plain, 1),
-            "speedup_saturated_vs_plain": round(sat / plain, 2), "slots": 6, "pool_fields": len(pool)}
+            "speedup_saturated_vs_plain": round(sat / plain, 2), "slots": slots,
+            "identical_outputs": bool(same), "compared": f"pairs and labels of {ncmp} requests, served vs plain",
+            "fields": "one per request (no reuse): GRF P(k)~k^-2.5, cubic side log-uniform in [32, 384]",
+            "resident": resident}
+
+
+def host_cpu() -> dict:
+    """CPU model (lscpu) and core count of this host."""
+    import platform
+
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": model, "machine": platform.machine(), "nproc": os.cpu_count()}
+
+
+def oracle_step(crop, t_thr) -> dict:
+    """One pass of the oracle over `crop`, each phase timed (seconds)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    order = oracle.sort_order(crop)
+    t1 = time.perf_counter()
+    W = oracle.sweep(crop, order)
+    t2 = time.perf_counter()
+    oracle.pairs(W)
+    t3 = time.perf_counter()
+    oracle.components(crop, t_thr)
+    t4 = time.perf_counter()
+    return {"sort": t1 - t0, "sweep": t2 - t1, "pairs": t3 - t2, "labels": t4 - t3, "total": t4 - t0}
 
 
 def cpu_baseline(f_dev, side: int):
     """The CPU oracle, as it stands, on a side^3 crop of the same field: one
-    host thread runs sort + sweep, pairs and labels."""
+    host thread runs sort + sweep, pairs and labels (each phase timed)."""
     import numpy as np
-
-    import oracle
 
     crop = f_dev[:side, :side, :side].contiguous().cpu().numpy()
     t_thr = float(np.median(crop[::7, ::7, ::7]))
-    t0 = time.perf_counter()
-    W = oracle.merge_tree(crop)
-    oracle.pairs(W)
-    oracle.components(crop, t_thr)
-    dt = time.perf_counter() - t0
+    ph = oracle_step(crop, t_thr)
+    dt = ph["total"]
+    # the two smaller configs in full, once each
+    from paper_2301_10838_gb300 import fields
+
+    small = {}
+    for name in ("white64", "grf256q12"):
+        g = fields.named_field(name, seed=1)
+        small[name] = {k: round(v, 3) for k, v in oracle_step(g, float(np.median(g))).items()}
     return {"value": round(crop.size / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{side}^3 corner crop of the benchmark field ({crop.size} vertices), "
-                      f"sort+sweep+pairs+labels, {dt:.2f} s"}
+                      f"sort+sweep+pairs+labels, {dt:.2f} s",
+            "phases_s": {k: round(v, 3) for k, v in ph.items()}, "host": host_cpu(),
+            "configs_s": small}
 
 
 # ------------------------------------------------------------- reference
@@ -602,7 +941,6 @@ def run_reference(args):
         return
     import numpy as np
 
-    import oracle
     from paper_2301_10838_gb300 import fields
 
     side = min(args.cpu_side, args.side)
@@ -623,16 +961,12 @@ def run_reference(args):
         gen = f"generated at {full.shape[0]}^3 on the host"
     t_thr = float(np.median(crop[::7, ::7, ::7]))
 
-    def step():
-        W = oracle.merge_tree(crop)
-        oracle.pairs(W)
-        oracle.components(crop, t_thr)
-
     for _ in range(args.warmup):
-        step()
+        oracle_step(crop, t_thr)
+    phases = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        phases.append(oracle_step(crop, t_thr))
     dt = time.perf_counter() - t0
     value = crop.size * args.steps / dt / 1e6
     sample = f"{side}^3 corner crop of the {WORKLOAD} field ({gen}), one host thread"
@@ -652,7 +986,9 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample,
                    "step": "oracle merge_tree + pairs + components(median)"},
-        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "phases_s": {k: round(sum(p[k] for p in phases) / len(phases), 3) for k in phases[0]},
+                         "host": host_cpu()},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -662,6 +998,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.wide_grid:
+        import torch
+
+        print(json.dumps({"wide_grid": bench_wide_grid(args.wide_grid, torch.device("cuda", 0))}), flush=True)
     else:
         run_ours(args)
 
