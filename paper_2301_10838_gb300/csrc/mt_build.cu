@@ -209,7 +209,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     uint32_t *hkey = reinterpret_cast<uint32_t *>(hlev + HS);
     uint32_t *hist = reinterpret_cast<uint32_t *>(hlev);          // key histogram (before the rounds)
     __shared__ uint8_t s_bmap[BINS];                              // histogram bin -> bucket
-    __shared__ uint32_t s_kmin, s_kmax, s_nvalid, s_warp[NT / 32];
+    __shared__ uint32_t s_nvalid, s_warp[NT / 32], s_wmin[NT / 32], s_wmax[NT / 32];
     __shared__ uint32_t s_boff[NB + 2], s_bcur[NB + 1], s_thr[NB];
 
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -226,13 +226,10 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     auto lzo = [](uint32_t l) { return l >> (LX + LY); };
     auto valid = [&](uint32_t l) { return FULL || (lxo(l) < wx && lyo(l) < wy && lzo(l) < wz); };
     auto gid = [&](uint32_t l) -> Id { return base + (Id)lzo(l) * nxy + (Id)lyo(l) * nx + lxo(l); };
-    if (threadIdx.x == 0) {
-        s_kmin = 0xFFFFFFFFu, s_kmax = 0;
-        s_nvalid = wx * wy * wz;
-    }
+    // (the barrier after the loads orders these writes before their uses)
+    if (threadIdx.x == 0) s_nvalid = wx * wy * wz;
     if (threadIdx.x <= NB) s_bcur[threadIdx.x] = 0;
     for (uint32_t i = threadIdx.x; i < (uint32_t)BINS; i += NT) hist[i] = 0;
-    __syncthreads();
 
     // 1. load the tile's values (rows of TX floats) as order keys
     bool bad = false;
@@ -267,16 +264,19 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
         kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
         kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
     }
-    if (lane == 0) {
-        atomicMin(&s_kmin, kmin);
-        atomicMax(&s_kmax, kmax);
-    }
+    if (lane == 0) s_wmin[warp] = kmin, s_wmax[warp] = kmax;
     __syncthreads();
+    kmin = lane < NT / 32 ? s_wmin[lane] : 0xFFFFFFFFu;
+    kmax = lane < NT / 32 ? s_wmax[lane] : 0u;
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
 
     // 2. seed: T[l] = (l, first vertex of the closed in-tile neighbourhood);
     //    key histogram for the level buckets
-    const uint32_t kmin_t = s_kmin;
-    const float bscale = (float)BINS / ((float)(s_kmax - kmin_t) + 1.0f);
+    const uint32_t kmin_t = kmin, kmax_t = kmax;
+    const float bscale = (float)BINS / ((float)(kmax_t - kmin_t) + 1.0f);
     auto bin_of = [&](uint32_t k) { return min((uint32_t)BINS - 1, (uint32_t)((float)(k - kmin_t) * bscale)); };
     for (uint32_t l = threadIdx.x; l < TV; l += NT) {
         if (!valid(l)) continue;
@@ -338,7 +338,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     // one compare in the shortcut climbs instead of the bin lookup. Read
     // only after the barriers that end step 4.
     if (threadIdx.x < (uint32_t)NB) {
-        uint32_t lo = kmin_t, hi = s_kmax + 1u;
+        uint32_t lo = kmin_t, hi = kmax_t + 1u;
         while (lo < hi) {
             const uint32_t mid = lo + (hi - lo) / 2;
             if (bucket_of(mid) >= threadIdx.x) hi = mid;
@@ -412,7 +412,43 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     volatile uint16_t *vSC = SC;
     volatile uint32_t *vHK = hkey;
     volatile unsigned long long *vHL = hlev;
-    for (int b = 0; b < NB; b++) {
+    // Round b's bucket repair (5c) runs in the same phase as round b+1's
+    // scan (5a), with no barrier between them. The scan of round b stores in
+    // every vertex of bucket b the round-b shortcut of its minimum, where its
+    // repair starts, so the repair needs no shortcut cache; its climbs follow
+    // links at or below the vertex's own level, which round b+1 never
+    // changes (its merges, in the hash-crowded case run during the scan,
+    // displace only links above bucket b). The scan reads the triplet of a
+    // lower neighbour that the repair may be rewriting: before, (w, minimum)
+    // or (w, shortcut); after, (w, representative) -- every one a vertex of
+    // w's component below the round, with the same shortcut.
+    for (int b = 0; b <= NB; b++) {
+        // 5c. final tile triplets of the inner vertices of bucket b - 1 (this
+        //     also clears their cross masks)
+        if (b > 0) {
+            for (uint32_t i = s_boff[b - 1] + threadIdx.x; i < s_boff[b]; i += NT) {
+                const uint32_t l = vlist[i];
+                uint32_t wr;
+                const uint32_t r = sm_climb<TV>(T, K, tid_v(vT[l]), l, K[l], wr, ok);
+                T[l] = sm_pack(l, r);
+            }
+        }
+        if (b == NB) {
+            // 6. repair the branch minima (Algorithm 5), beside the last
+            //    bucket repair: both only follow links of minima, and a
+            //    minimum's repair moves its target along its own chain below
+            //    its own saddle, which leaves every climb's result unchanged
+            for (uint32_t i = s_boff[NB] + threadIdx.x; i < s_boff[NB + 1]; i += NT) {
+                const uint32_t l = vlist[i];
+                const uint32_t w = vT[l];
+                const uint32_t s = sm_s(w);
+                if (s == l) continue;  // inner vertex or root
+                uint32_t wr;
+                const uint32_t r = sm_climb<TV>(T, K, sm_v(w), s, K[s], wr, ok);
+                if (r != sm_v(w)) T[l] = sm_pack(s, r);
+            }
+            break;
+        }
         // shortcut of minimum m for round b: climb through the links whose
         // saddle lies in an earlier bucket, from where round (SC >> IDB) left it
         auto shortcut = [&](uint32_t m) -> uint32_t {
@@ -427,23 +463,25 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
             vSC[m] = (uint16_t)(((uint32_t)b << IDB) | x);
             return x;
         };
-        const uint32_t i0 = s_boff[b], i1 = s_boff[b + 1];
         // 5a. scan the cross edges whose upper end S lies in bucket b; collect
         //     those whose ends are not yet known to be connected below S,
-        //     one per pair of shortcuts (the earliest S)
-        for (uint32_t i = i0 + threadIdx.x; i < i1; i += NT) {
+        //     one per pair of shortcuts (the earliest S); store every
+        //     vertex's shortcut for its repair
+        for (uint32_t i = s_boff[b] + threadIdx.x; i < s_boff[b + 1]; i += NT) {
             const uint32_t S = vlist[i];
             const uint32_t TSw = vT[S];
             uint32_t m = xmask(TSw);
+            const uint32_t aS = shortcut(tid_v(TSw));
+            vT[S] = sm_pack(S, aS);
             if (m == 0) continue;
             const uint32_t kS = K[S];
-            const uint32_t aS = shortcut(tid_v(TSw));
             do {
                 const uint32_t d = __ffs(m) - 1;
                 m &= m - 1;
                 const uint32_t w = nbr(S, d);
                 const uint32_t Tw = vT[w];
-                // w's minimum: an inner vertex's target, else w itself
+                // a vertex of w's component below the round: an inner
+                // vertex's target, else w itself
                 const uint32_t dw = (tid_s(Tw) == w && tid_v(Tw) != w) ? tid_v(Tw) : w;
                 const uint32_t aw = shortcut(dw);
                 if (aw == aS) continue;  // already connected below S
@@ -474,26 +512,6 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
             sm_merge<TV>(T, K, (uint32_t)lev, (uint32_t)(lev >> 32), pr >> IDB, pr & IDM, ok);
         }
         __syncthreads();
-        // 5c. final tile triplets of the inner vertices of bucket b (this
-        //     also clears their cross masks)
-        for (uint32_t i = i0 + threadIdx.x; i < i1; i += NT) {
-            const uint32_t l = vlist[i];
-            uint32_t wr;
-            const uint32_t r = sm_climb<TV>(T, K, shortcut(tid_v(vT[l])), l, K[l], wr, ok);
-            T[l] = sm_pack(l, r);
-        }
-        __syncthreads();
-    }
-
-    // 6. repair the branch minima (Algorithm 5)
-    for (uint32_t i = s_boff[NB] + threadIdx.x; i < s_boff[NB + 1]; i += NT) {
-        const uint32_t l = vlist[i];
-        const uint32_t w = vT[l];
-        const uint32_t s = sm_s(w);
-        if (s == l) continue;  // inner vertex or root
-        uint32_t wr;
-        const uint32_t r = sm_climb<TV>(T, K, sm_v(w), s, K[s], wr, ok);
-        if (r != sm_v(w)) T[l] = sm_pack(s, r);
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
     __syncthreads();
