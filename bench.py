@@ -376,6 +376,14 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(f, args.cpu_side)
+        try:
+            omp = openmp_baseline(f, W)
+            gpu_build = sum(phases[k][1] for k in ("tile", "merge", "repair") if k in phases) / args.steps
+            omp["gpu_build_ms"] = round(gpu_build, 3)
+            omp["gpu_speedup_over_openmp_build"] = round(omp["build_s"] * 1e3 / gpu_build, 1)
+            cpu["openmp_tmt"] = omp
+        except (OSError, RuntimeError, subprocess.CalledProcessError) as e:
+            cpu["openmp_tmt"] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
     del W, labels, pairs, ws
     f = None
     torch.cuda.empty_cache()
@@ -907,6 +915,33 @@ def oracle_step(crop, t_thr) -> dict:
     oracle.components(crop, t_thr)
     t4 = time.perf_counter()
     return {"sort": t1 - t0, "sweep": t2 - t1, "pairs": t3 - t2, "labels": t4 - t3, "total": t4 - t0}
+
+
+def openmp_baseline(f_dev, W_dev) -> dict:
+    """The paper's parallel algorithm on all host cores with OpenMP (the
+    counterpart of its OpenMP runs, Table 1) on the whole benchmark field,
+    its triplets compared with the GPU's."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    full = f_dev.contiguous().cpu().numpy()
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    W = oracle.tmt_openmp(full, threads)
+    dt = time.perf_counter() - t0
+    same = True
+    flat = W_dev.reshape(-1)
+    step = 1 << 27
+    for a in range(0, flat.numel(), step):
+        got = flat[a:a + step].cpu().numpy().view(np.uint64)
+        same &= bool(np.array_equal(got, W[a:a + step]))
+    del W
+    torch.cuda.synchronize()
+    return {"value": round(full.size / dt / 1e6, 2), "unit": UNIT, "threads": threads, "build_s": round(dt, 2),
+            "sample": "the whole benchmark field: seed (u, u), every edge merged with 64-bit CAS, repair",
+            "equals_gpu_triplets": same}
 
 
 def cpu_baseline(f_dev, side: int):

@@ -20,6 +20,9 @@ Functions
   simplified_components(f, W, t, eps) -> labels of G_t after filling every
                            branch of persistence < eps up to its saddle
   branches(f, W)           -> (order, offsets): vertices grouped by branch
+  tmt_openmp(f, threads)   -> W from the paper's parallel algorithm on the
+                           host cores with OpenMP (tmt_openmp.c): a CPU
+                           baseline beside the oracle, not the oracle
   merge_tree_wide(f), pairs_wide(W2), components_wide(f, t),
   point_triplet_wide(f, u, budget)   the same with 64-bit ids: W2 is
                            uint64[n, 2] = (s, v), pairs uint64[k, 2], labels
@@ -298,3 +301,40 @@ def point_triplet_wide(f, u: int, budget: int = 1 << 20):
     if r < 0:
         raise OracleError(r)
     return (int(out[0]), int(out[1])) if r == 1 else None
+
+
+# ---- CPU baseline: the paper's parallel algorithm with OpenMP (not the oracle)
+
+_OMP_SRC = os.path.join(_HERE, "tmt_openmp.c")
+_OMP_LIB = os.path.join(_BUILD, "libtmt_openmp.so")
+_omp = None
+
+
+def build_openmp(force: bool = False) -> str:
+    """Compile tmt_openmp.c (gcc -fopenmp) into oracle/_build/libtmt_openmp.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = force or not os.path.exists(_OMP_LIB) or os.path.getmtime(_OMP_LIB) < os.path.getmtime(_OMP_SRC)
+    if stale:
+        tmp = _OMP_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _OMP_SRC, "-lm"])
+        os.replace(tmp, _OMP_LIB)
+    return _OMP_LIB
+
+
+def tmt_openmp(f, threads: int | None = None) -> np.ndarray:
+    """Triplets W[u] = (s << 32) | v from Algorithm 1 of the paper run in
+    parallel on `threads` host cores (default: all), seeded with (u, u), every
+    edge merged with a 64-bit compare-and-swap, then repaired. The result is
+    unique, so it equals merge_tree(f); the tests check that."""
+    global _omp
+    with _lock:
+        if _omp is None:
+            lib = ctypes.CDLL(build_openmp())
+            lib.tmt_openmp.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_int, ctypes.c_void_p]
+            lib.tmt_openmp.restype = ctypes.c_int
+            _omp = lib
+    f, nx, ny, nz = _field(f)
+    W = np.empty(f.size, dtype=np.uint64)
+    _check(_omp.tmt_openmp(_ptr(f), nx, ny, nz, int(threads or os.cpu_count() or 1), _ptr(W)))
+    return W

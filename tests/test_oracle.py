@@ -391,3 +391,37 @@ def test_sin_product_closed_form(seed):
     assert starts == want
     p, roots = oracle.pairs(W)
     assert len(p) == count - 1 and len(roots) == 1
+
+
+def test_openmp_baseline_equals_oracle():
+    """The CPU baseline (the paper's parallel algorithm with OpenMP, lock-free
+    merges racing on 4 and 8 threads) gives the oracle's unique triplets on
+    grids with ties, signed zeros, plateaus and monotone ramps."""
+    rng = np.random.default_rng(8)
+    cases = []
+    for i in range(40):
+        shape = tuple(int(x) for x in rng.integers(1, 20, size=3))
+        k = i % 4
+        if k == 0:
+            f = rng.random(shape, dtype=np.float32)
+        elif k == 1:
+            f = rng.integers(0, 5, size=shape).astype(np.float32)
+        elif k == 2:
+            f = rng.choice(np.array([-0.0, 0.0, -1.0, 3.0], np.float32), size=shape)
+        else:
+            f = rng.random(shape, dtype=np.float32)
+            f[..., : shape[2] // 2] = 0.5
+        cases.append(f)
+    nz = ny = nx = 12
+    cases.append(np.add.outer(np.add.outer(np.arange(nz), np.arange(ny)), np.arange(nx)).astype(np.float32))
+    cases.append(fields_grf_like(rng))
+    for f in cases:
+        want = oracle.merge_tree(f)
+        for threads in (4, 8):
+            assert np.array_equal(oracle.tmt_openmp(f, threads), want), f.shape
+
+
+def fields_grf_like(rng):
+    from paper_2301_10838_gb300 import fields
+
+    return fields.quantize(fields.grf((24, 20, 28), -3.0, int(rng.integers(0, 1000))), 128)
