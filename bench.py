@@ -4,10 +4,14 @@
 
 One step is one pass of the whole hot path over the 1024^3 lognormal field
 exp(0.8 g) (g a Gaussian random field with P(k) ~ k^-2, float32, seed 1+rank):
-  mt_build_triplets_cfg (validate, init, descent jumping, merge, repair; the
-                         launch configuration the autotuner picks)
+  mt_build_components   (validate, init, descent jumping, merge, repair with
+                         the labels of G_t at the field's median value taken
+                         inside the repair pass; the launch configuration the
+                         autotuner picks)
   mt_persistence_pairs  (ordered pair compaction; synchronises)
-  mt_components_at      (labels of G_t at the field's median value)
+--separate times the same work as three calls (mt_build_triplets_cfg,
+mt_persistence_pairs, mt_components_at); either way the line reports the
+other form too ("other_step_form").
 The field (4 GiB) and triplets (8 GiB) are far larger than the 129 MB L2, so
 no flush is needed between steps. Timing uses CUDA events on the launching
 stream, W untimed warm-up steps, barrier + synchronize on both sides, max over
@@ -54,6 +58,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the split tree, branches and small configs")
     ap.add_argument("--wide-grid", default="", help="nx,ny,nz: also time the wide-id path on this grid alone")
     ap.add_argument("--cfg", type=int, default=-1, help="launch configuration to use instead of autotuning")
+    ap.add_argument("--separate", action="store_true",
+                    help="time build, pairs and labels as three calls (default: labels inside the build)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
@@ -125,14 +131,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ algorithmic bytes
-def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 32)) -> dict:
+def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 32), fused: bool = True) -> dict:
     """Bytes the method must move per step, by kernel:
       tile    init: read f (4n) + write W (8n); plus two triplet reads per
               merged edge inside the tiles, 16 (E' - C)
       merge   (k_cross) two triplet reads per edge between tiles: 16 C
-      repair  read + write W (16n)
+      repair  read + write W (16n); labelling inside it (fused): + read f
+              (4n) + write labels (4n)
       pairs   scan W (8n) + write pairs (8 npairs)
-      labels  read f (4n) + W (8n), write labels (4n)
+      labels  (separate pass) read f (4n) + W (8n), write labels (4n)
     E' = E - (n - #minima) (edges that are not steepest-descent seeds: the
     per-edge cost of the edge loop of Algorithm 1) and C the edges between
     tiles; tile + merge together are 12n + 16E'.
@@ -143,8 +150,9 @@ def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 32)) -> dict:
     nmin = npairs + 1
     Ep = E - (n - nmin)
     C = ((nx - 1) // tx) * ny * nz + ((ny - 1) // ty) * nx * nz + ((nz - 1) // tz) * nx * ny
-    return {"tile": 12 * n + 16 * (Ep - C), "merge": 16 * C, "repair": 16 * n, "pairs": 8 * n + 8 * npairs,
-            "labels": 16 * n, "E": E, "E_prime": Ep, "cross_edges": C}
+    return {"tile": 12 * n + 16 * (Ep - C), "merge": 16 * C, "repair": 24 * n if fused else 16 * n,
+            "pairs": 8 * n + 8 * npairs, "labels": 0 if fused else 16 * n, "E": E, "E_prime": Ep,
+            "cross_edges": C}
 
 
 def traffic_record(kernel: str) -> dict:
@@ -245,12 +253,22 @@ def run_ours(args):
     pairs = torch.empty((npairs, 2), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    # one step: the build with the labels of G_t taken inside its repair pass,
+    # then the pairs (--separate: build, pairs and labels as three calls)
+    fused = not args.separate
+
+    def step_separate():
         mt.mt_build_triplets_cfg(f, W, ws, 0, cfg)
         np_, root = mt.mt_persistence_pairs(f, W, pairs, ws)
         mt.mt_components_at(f, W, t_thr, labels, ws)
         return np_
 
+    def step_fused():
+        mt.mt_build_components(f, W, t_thr, labels, ws, cfg=cfg)
+        np_, root = mt.mt_persistence_pairs(f, W, pairs, ws)
+        return np_
+
+    step = step_fused if fused else step_separate
     for _ in range(args.warmup):
         step()
     mt.mt_sync_status(ws)
@@ -284,9 +302,29 @@ def run_ours(args):
     ms_step = ms_total / args.steps
     value = job_rate(world, n, args.steps, ms_total)
 
+    # the other form of the step, timed the same way, for comparison
+    other = step_separate if fused else step_fused
+    other()
+    mt.mt_trace_enable(True)
+    mt.mt_trace_read(reset=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        other()
+    ev1.record(stream)
+    barrier()
+    other_phases = mt.mt_trace_read(reset=True)
+    mt.mt_trace_enable(False)
+    mt.mt_sync_status(ws)
+    other_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+    other_step = {"step": "mt_build_triplets_cfg + mt_persistence_pairs + mt_components_at" if fused
+                  else "mt_build_components + mt_persistence_pairs",
+                  "ms_per_step": round(other_ms, 3),
+                  "phases_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in other_phases.items()}}
+
     # roofline of the dominant kernel family from the live phase timing
     peak, peak_kind = measured_peaks()
-    ab = algorithmic_bytes(n, shape, npairs)
+    ab = algorithmic_bytes(n, shape, npairs, fused=fused)
     dom = max((k for k in phases if k in ab), key=lambda k: phases[k][1])
     calls, tot = phases[dom]
     achieved = ab[dom] / (tot / calls / 1e3) / 1e9
@@ -331,8 +369,11 @@ def run_ours(args):
         def e2e_step(k, last):
             df, dW, dl, dp, dws = bufs[k % depth]
             s_cmp.wait_event(loaded[k % depth])
-            mt.mt_build_triplets_cfg(df, dW, dws, 0, cfg, stream=s_cmp)
-            mt.mt_components_at(df, dW, t_thr, dl, dws, stream=s_cmp)
+            if fused:
+                mt.mt_build_components(df, dW, t_thr, dl, dws, cfg=cfg, stream=s_cmp)
+            else:
+                mt.mt_build_triplets_cfg(df, dW, dws, 0, cfg, stream=s_cmp)
+                mt.mt_components_at(df, dW, t_thr, dl, dws, stream=s_cmp)
             built = torch.cuda.Event()
             built.record(s_cmp)
             s_out.wait_event(built)
@@ -411,7 +452,9 @@ def run_ours(args):
                 "grid": [shape[2], shape[1], shape[0]],
                 "field": "exp(0.8 g), g unit-variance GRF P(k)~k^-2, float32, seed 1+rank",
                 "field_sha256": field_sha,
-                "step": "mt_build_triplets_cfg(tuned cfg) + mt_persistence_pairs + mt_components_at(median)",
+                "step": ("mt_build_components(tuned cfg, median: labels inside the repair pass) + "
+                         "mt_persistence_pairs") if fused else
+                        "mt_build_triplets_cfg(tuned cfg) + mt_persistence_pairs + mt_components_at(median)",
                 "build_cfg": cfg,
                 "threshold": t_thr,
                 "npairs": npairs,
@@ -430,6 +473,7 @@ def run_ours(args):
             "step_roofline": {"algorithmic_bytes": step_bytes,
                               "frac": round(step_bytes / (ms_step / 1e3) / 1e9 / peak, 4)},
             "phases_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in phases.items()},
+            "other_step_form": other_step,
             "autotune": ({"shape_class": autotune.single_class(shape), "chosen_cfg": cfg,
                           "build_ms_by_cfg": {str(k): round(v, 3) for k, v in tune_ms.items()},
                           "default_cfg_ms": round(tune_ms[0], 3), "tuned_cfg_ms": round(tune_ms[cfg], 3)}
@@ -470,7 +514,7 @@ def _events_ms(fn, reps: int, dev, flush=None) -> list[float]:
 
 def bench_config(name: str, dev, peak: float) -> dict:
     """One of the smaller configs (64^3 white noise, 256^3 quantised GRF):
-    the same step as the benchmark (build + pairs + labels at the median),
+    the same step as the benchmark (build with labels at the median + pairs),
     L2 flushed (a 256 MiB write) before each step, median of 9 steps."""
     import numpy as np
     import torch
@@ -491,9 +535,8 @@ def bench_config(name: str, dev, peak: float) -> dict:
     cfg, tune_ms = autotune.tune_single(f, W, ws, use_cache=False)
 
     def step():
-        mt.mt_build_triplets_cfg(f, W, ws, 0, cfg)
+        mt.mt_build_components(f, W, t, labels, ws, cfg=cfg)
         state["k"], _ = mt.mt_persistence_pairs(f, W, pairs, ws)
-        mt.mt_components_at(f, W, t, labels, ws)
 
     for _ in range(3):
         step()

@@ -174,6 +174,21 @@ mt_status mt_simplified_components_at(const float *d_f, const uint64_t *d_W, mt_
                                       uint32_t flags, uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
+ * One build that also labels the components of G_t: the triplets of
+ * mt_build_triplets_cfg(d_f, g, d_W, d_ws, ws_bytes, flags, cfg, stream) and
+ * the labels of mt_simplified_components_at(d_f, d_W, g, t, eps, flags,
+ * d_labels, ...) (eps <= 0: those of mt_components_at_ex), bit for bit. The
+ * labels are read off the tree inside the repair pass (Algorithm 4 with the
+ * value test f(s) <= t, continued from where Algorithm 5 leaves each walk),
+ * which saves the separate labelling pass over the field and the triplets.
+ *   d_labels  uint32[n], 4-byte aligned, output.  t and eps must not be NaN.
+ * Arguments, flags, cfg and errors otherwise as mt_build_triplets_cfg.
+ * Asynchronous.
+ */
+mt_status mt_build_components(const float *d_f, mt_grid g, uint64_t *d_W, float t, float eps, uint32_t flags,
+                              uint32_t cfg, uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream);
+
+/*
  * Branch decomposition (Section 2.1: every vertex lies on one branch of the
  * tree; the CPU implementation of Section 3.1 keeps each branch's vertices in
  * a list beside its triplets). A minimum u (W[u].s != u, or the root) heads

@@ -37,6 +37,7 @@ __all__ = [
     "mt_build_triplets_ex",
     "mt_build_triplets_cfg",
     "mt_build_autotune",
+    "mt_build_components",
     "MT_CFG_SMALL_TILES",
     "MT_CFG_FOUR_ROUNDS",
     "MT_CFG_REPAIR_256",
@@ -124,6 +125,8 @@ _SIGS = {
     "mt_build_triplets_cfg": ([_P, Grid, _P, _P, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint32, _P],
                               ctypes.c_int32),
     "mt_build_autotune": ([_P, Grid, _P, _P, ctypes.c_size_t, ctypes.c_uint32, _P, _P, _P], ctypes.c_int32),
+    "mt_build_components": ([_P, Grid, _P, ctypes.c_float, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, _P, _P,
+                             ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_components_at_ex": ([_P, _P, Grid, ctypes.c_float, ctypes.c_uint32, _P, _P, ctypes.c_size_t, _P],
                             ctypes.c_int32),
     "mt_persistence_pairs_noalloc": ([_P, _P, Grid, _P, _U64, _P, _P, _P], ctypes.c_int32),
@@ -294,6 +297,19 @@ def mt_build_autotune(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, flags:
                                     _dev(ws, "ws", (torch.uint8,)), ws.numel(), int(flags), _stream_ptr(stream),
                                     ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(best)), "mt_build_autotune")
     return {c: float(ms[i]) for i, c in enumerate((0, 2, 4, 6))}, int(best.value)
+
+
+def mt_build_components(f: torch.Tensor, W: torch.Tensor, t: float, labels: torch.Tensor, ws: torch.Tensor,
+                        eps: float = 0.0, flags: int = 0, cfg: int = 0, stream=None) -> None:
+    """One build that also labels G_t: the triplets of mt_build_triplets_cfg
+    and the labels of mt_simplified_components_at (eps <= 0: those of
+    mt_components_at_ex), the labels taken inside the repair pass."""
+    g = grid_of(f)
+    n = f.numel()
+    _check(load().mt_build_components(_dev(f, "f", (torch.float32,)), g, _dev(W, "W", _I64, n), float(t), float(eps),
+                                      int(flags), int(cfg), _dev(labels, "labels", _I32, n),
+                                      _dev(ws, "ws", (torch.uint8,)), ws.numel(), _stream_ptr(stream)),
+           "mt_build_components")
 
 
 def mt_components_at_ex(f: torch.Tensor, W: torch.Tensor, t: float, flags: int, labels: torch.Tensor,

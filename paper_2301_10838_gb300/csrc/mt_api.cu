@@ -167,6 +167,28 @@ mt_status mt_build_triplets_cfg(const float *d_f, mt_grid g, uint64_t *d_W, void
     return MT_OK;
 }
 
+mt_status mt_build_components(const float *d_f, mt_grid g, uint64_t *d_W, float t, float eps, uint32_t flags,
+                              uint32_t cfg, uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream)
+{
+    if (cfg >= MT_CFG_COUNT || (cfg & MT_CFG_SMALL_TILES)) return MT_ERR_INVALID;
+    uint64_t n;
+    mt_status st = grid_n(g, n);
+    if (st != MT_OK) return st;
+    if (!d_f || !d_W || !d_labels || std::isnan(t) || std::isnan(eps) || ((uintptr_t)d_f & 3) ||
+        ((uintptr_t)d_W & 7) || ((uintptr_t)d_labels & 3) || (flags & ~MT_SUPERLEVEL))
+        return MT_ERR_INVALID;
+    Workspace ws;
+    if (ws_bytes < build_workspace_bytes(g.nx, g.ny, g.nz) || !carve_workspace(d_ws, ws_bytes, n, ws))
+        return MT_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws.status, 0, 256, s) != cudaSuccess) return MT_ERR_CUDA;
+    const float sg = (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f;
+    const LabelArgs la{d_labels, sg * t, eps};
+    if (launch_build(d_f, d_W, g.nx, g.ny, g.nz, ws, build_faces(d_ws, n), sg, s, cfg, &la) != cudaSuccess)
+        return MT_ERR_CUDA;
+    return MT_OK;
+}
+
 mt_status mt_build_autotune(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
                             void *stream, float *ms, uint32_t *best)
 {

@@ -3,7 +3,8 @@
 //              lowest lower neighbour, descent pointer jumping, Merge of the
 //              in-tile edges, Repair
 //   k_cross    Merge (Algorithm 3) of the edges between tiles, 64-bit CAS
-//   k_repair   Repair (Algorithm 5) via Representative (Algorithm 4)
+//   k_repair   Repair (Algorithm 5) via Representative (Algorithm 4); in
+//              mt_build_components also the components of G_t
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -727,6 +728,20 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
 // loads of a thread overlap. A branch minimum that finds the list full is
 // repaired on the spot in step 1; a target without a slot (hash or copies
 // full) is chased along the global chain in step 4.
+//
+// With LAB the pass also labels the components of G_t (the labels of
+// k_labels) where it already stands. The representative of u at level t is
+// the end of the walk from u along links with f(s) <= t (Algorithm 4 with a
+// value test). Any valid triplet forest gives the same end, repaired or not:
+// a walk stops at the first link above t, and every link it passes joins two
+// vertices of one component of G_t, the second deeper. So a branch minimum
+// continues the walk from its repaired target when its saddle is at or below
+// t (step 3), every copied chain gives its target's label by a search of the
+// copy for t, shared by all inner vertices of the target (step 3), and step 4
+// writes every vertex's label: 0xFFFFFFFF above t, the copy's label, or a
+// global walk for a target without a copy. Concurrent repairs move entries
+// along their own chains below their own saddles, which keeps every walk's
+// end.
 template <int LX, int LY, int LZ>
 struct RepairShape {
     static constexpr uint32_t TV = 1u << (LX + LY + LZ);
@@ -736,10 +751,11 @@ struct RepairShape {
     static constexpr uint32_t kList = TV / 4 / kRepairShrink;   // branch minima listed
     static constexpr size_t kSmem =
         (size_t)kCap * kHops * 12 + (size_t)kHash * 4 + (size_t)kHash * 2 + (size_t)kList * 2;
+    static constexpr size_t kSmemLab = kSmem + (size_t)kCap * 4;  // + each copy's label
 };
 
-template <int LX, int LY, int LZ, int NT, class Loc>
-__global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
+template <int LX, int LY, int LZ, int NT, class Loc, bool LAB>
+__global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, const LabelArgs la)
 {
     if (block_skips(status)) return;
     using RS = RepairShape<LX, LY, LZ>;
@@ -757,7 +773,8 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
     uint32_t *ek = es + CAP * H;
     uint32_t *ev = ek + CAP * H;
     uint32_t *hkey = ev + CAP * H;             // hashed targets
-    uint16_t *hslot = reinterpret_cast<uint16_t *>(hkey + HS);  // their copy slots
+    uint32_t *slab = hkey + HS;                // LAB: label at t of each copy's target
+    uint16_t *hslot = reinterpret_cast<uint16_t *>(slab + (LAB ? CAP : 0));  // copy slots of the targets
     uint16_t *list = hslot + HS;               // branch minima (tile-local ids)
     __shared__ uint32_t s_nmin, s_ncopy;
 
@@ -791,12 +808,38 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
         return HS;
     };
 
+    bool ok = true;
+    constexpr uint32_t OUT = 0xFFFFFFFFu;  // label of a vertex outside G_t (or in a filled pit)
+    const float lt = la.t;
+    // representative at t: the walk along links with f(s) <= t
+    auto rep_at_t = [&](uint32_t x) -> uint32_t {
+        for (uint32_t h = 0;; h++) {
+            const uint64_t T = W[x];
+            const uint32_t s = tri_s(T), v = tri_v(T);
+            if ((s == x && v == x) || !(f[s] <= lt)) return x;
+            x = v;
+            if (h >= kChaseLimit) {
+                ok = false;
+                return x;
+            }
+        }
+    };
+    // with eps > 0: 0xFFFFFFFF for a representative heading a branch of
+    // persistence below eps (its component lies in a filled pit)
+    auto simplified = [&](uint32_t r) -> uint32_t {
+        if (!(la.eps > 0.0f)) return r;
+        const uint32_t s = tri_s(W[r]);
+        if (s == r) return r;  // the root
+        return f[s] - f[r] >= la.eps ? r : OUT;
+    };
+    // label of branch minimum m (saddle s) whose link leads to r
+    auto min_label = [&](uint32_t m, float fs, uint32_t r) { return simplified(fs <= lt ? rep_at_t(r) : m); };
+
     for (uint32_t i = threadIdx.x; i < HS; i += NT) hkey[i] = EMPTY;
     if (threadIdx.x == 0) s_nmin = 0, s_ncopy = 0;
     __syncthreads();
 
     // 1. scan
-    bool ok = true;
     volatile uint32_t *vhk = hkey;
     for (uint32_t l0 = 0; l0 < TV; l0 += NT * NB) {
         uint64_t Tb[NB];
@@ -830,9 +873,11 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
                     list[pos] = (uint16_t)l;
                 } else if (is_min) {  // list full: repair this branch minimum now
                     uint32_t steps = 0;
-                    const uint32_t r = representative_cached(W, f, v, s, f[s], steps);
+                    const float fs = f[s];
+                    const uint32_t r = representative_cached(W, f, v, s, fs, steps);
                     if (steps > kChaseLimit) ok = false;
                     else if (r != v) st_tri(W + u, tri_pack(s, r));
+                    if (LAB) la.labels[u] = min_label(u, fs, r);
                 }
             }
         }
@@ -856,9 +901,11 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
             const uint64_t T = W[u];
             const uint32_t s = tri_s(T), t = tri_v(T);
             uint32_t steps = 0;
-            const uint32_t r = representative_cached(W, f, t, s, f[s], steps);
+            const float fs = f[s];
+            const uint32_t r = representative_cached(W, f, t, s, fs, steps);
             if (steps > kChaseLimit) ok = false;
             else if (r != t) st_tri(W + u, tri_pack(s, r));
+            if (LAB) la.labels[u] = min_label(u, fs, r);  // 0xFFFFFFFF above t: step 4
             continue;
         }
         const uint32_t h = i - nmin;
@@ -891,6 +938,15 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
         // where a vertex above it goes on along the global chain
         const uint32_t ps = ended ? END : es[b + j - 1], pk = ended ? END : ek[b + j - 1];
         for (; j < H; j++) es[b + j] = ps, ek[b + j] = pk, ev[b + j] = x;
+        if (LAB) {
+            // links of the copy at or below t (saddle values; END is above
+            // every finite key); past the whole copy the walk goes on globally
+            const uint32_t kt = order_key(lt);
+            uint32_t lo = 0;
+            while (lo < H && ek[b + lo] <= kt) lo++;
+            const uint32_t r = lo ? ev[b + lo - 1] : x0v;
+            slab[hslot[h]] = simplified(lo == H ? rep_at_t(r) : r);
+        }
     }
     __syncthreads();
 
@@ -911,7 +967,13 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
             const uint32_t l = l0 + k * NT + threadIdx.x;
             const uint32_t u = gid_of(l);
             const uint32_t s = tri_s(Tb[k]), t = tri_v(Tb[k]);
-            if (s != u || t == u) continue;
+            if (s != u || t == u) {  // a branch minimum, the root, or outside the grid
+                if (LAB && inside(l)) {
+                    if (!(fb[k] <= lt)) la.labels[u] = OUT;
+                    else if (s == u) la.labels[u] = u;  // the root labels itself
+                }
+                continue;
+            }
             const uint32_t h = find(t);
             const uint16_t c = h < HS ? hslot[h] : NOSLOT;
             uint32_t r = t;
@@ -937,6 +999,8 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status)
                 }
             }
             if (r != t) st_tri(W + u, tri_pack(u, r));
+            // t >= f(u): the walk at t passes the representative at u
+            if (LAB) la.labels[u] = !(fb[k] <= lt) ? OUT : c != NOSLOT ? slab[c] : simplified(rep_at_t(r));
         }
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
@@ -994,15 +1058,16 @@ static cudaError_t tile_attrs()
     return cudaSuccess;
 }
 
-template <int V, int NT, class Loc>
+template <int V, int NT, class Loc, bool LAB>
 static cudaError_t repair_attrs()
 {
     using VV = Variant<V>;
+    using RS = RepairShape<VV::LX, VV::LY, VV::LZ>;
     static bool done = false;  // per instantiation
     if (done) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(k_repair<VV::LX, VV::LY, VV::LZ, NT, Loc>,
+    const cudaError_t e = cudaFuncSetAttribute(k_repair<VV::LX, VV::LY, VV::LZ, NT, Loc, LAB>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)RepairShape<VV::LX, VV::LY, VV::LZ>::kSmem);
+                                               (int)(LAB ? RS::kSmemLab : RS::kSmem));
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -1035,14 +1100,16 @@ static cudaError_t launch_tile(const Loc &loc, uint32_t ntiles, uint32_t *queue,
     return cudaGetLastError();
 }
 
-template <int V, int NT, class Loc>
-static cudaError_t launch_repair(const Loc &loc, uint32_t ntiles, uint32_t *status, cudaStream_t st)
+template <int V, int NT, class Loc, bool LAB = false>
+static cudaError_t launch_repair(const Loc &loc, uint32_t ntiles, uint32_t *status, cudaStream_t st,
+                                 const LabelArgs &la = LabelArgs{})
 {
     using VV = Variant<V>;
     using RS = RepairShape<VV::LX, VV::LY, VV::LZ>;
     cudaError_t e;
-    if ((e = repair_attrs<V, NT, Loc>()) != cudaSuccess) return e;
-    k_repair<VV::LX, VV::LY, VV::LZ, NT, Loc><<<ntiles, NT, RS::kSmem, st>>>(loc, status);
+    if ((e = repair_attrs<V, NT, Loc, LAB>()) != cudaSuccess) return e;
+    k_repair<VV::LX, VV::LY, VV::LZ, NT, Loc, LAB><<<ntiles, NT, LAB ? RS::kSmemLab : RS::kSmem, st>>>(loc, status,
+                                                                                                   la);
     count_launch();
     return cudaGetLastError();
 }
@@ -1053,7 +1120,7 @@ static cudaError_t launch_repair(const Loc &loc, uint32_t ntiles, uint32_t *stat
 // configuration gives the same triplets.
 template <int V, class Loc>
 static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, int persistent_grid, bool full,
-                             uint32_t *status, cudaStream_t st, uint32_t cfg)
+                             uint32_t *status, cudaStream_t st, uint32_t cfg, const LabelArgs *la = nullptr)
 {
     using VV = Variant<V>;
     cudaError_t e;
@@ -1071,12 +1138,17 @@ static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, i
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     PhaseScope ps(kRepair, st);
+    if constexpr (std::is_same<Loc, OneField>::value) {  // labels only for a single field
+        if (la)
+            return (cfg & MT_CFG_REPAIR_256) ? launch_repair<V, 256, Loc, true>(loc, ntiles, status, st, *la)
+                                             : launch_repair<V, 512, Loc, true>(loc, ntiles, status, st, *la);
+    }
     return (cfg & MT_CFG_REPAIR_256) ? launch_repair<V, 256>(loc, ntiles, status, st)
                                      : launch_repair<V, 512>(loc, ntiles, status, st);
 }
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         uint32_t *faces, float sg, cudaStream_t st, uint32_t cfg)
+                         uint32_t *faces, float sg, cudaStream_t st, uint32_t cfg, const LabelArgs *la)
 {
     using VV = Variant<0>;
     OneField loc;
@@ -1092,7 +1164,7 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
     const uint32_t ntz = (nz + (1u << VV::LZ) - 1) >> VV::LZ;
     const uint64_t ntiles = (uint64_t)loc.d.ntx * loc.d.nty * ntz;
     const bool full = nx % (1u << VV::LX) == 0 && ny % (1u << VV::LY) == 0 && nz % (1u << VV::LZ) == 0;
-    return run_build<0>(loc, (uint32_t)ntiles, nullptr, 0, full, ws.status, st, cfg);
+    return run_build<0>(loc, (uint32_t)ntiles, nullptr, 0, full, ws.status, st, cfg, la);
 }
 
 // The tile kernel with 64-bit ids and 128-bit output words (the wide path):

@@ -29,6 +29,14 @@ struct FieldDesc {
     float sg = 1.0f;   // -1: the tree of -f (superlevel sets)
 };
 
+// Components of G_t read off the tree inside the repair pass of a build
+// (mt_build_components): labels[u] as mt_simplified_components_at gives it.
+struct LabelArgs {
+    uint32_t *labels;  // uint32[n]
+    float t;           // threshold on the values the order sees (sg * f)
+    float eps;         // persistence simplification; <= 0: none
+};
+
 // Views into the caller's workspace (layout fixed by carve_workspace).
 struct Workspace {
     uint32_t *status;  // status bits (ST_*)
@@ -71,8 +79,10 @@ int device_sms();
 cudaError_t readback(const uint64_t *meta, const uint32_t *status, cudaStream_t st, uint64_t out[4]);
 mt_status status_from_bits(uint32_t bits);
 
+// la: also label the components of G_t (null: triplets only)
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         uint32_t *faces, float sg, cudaStream_t st, uint32_t cfg = 0);
+                         uint32_t *faces, float sg, cudaStream_t st, uint32_t cfg = 0,
+                         const LabelArgs *la = nullptr);
 // f, sg, eps: persistence simplification (pairs of persistence below eps
 // dropped; eps <= 0 keeps all and does not read f)
 cudaError_t launch_pairs(const uint64_t *W, uint64_t n, uint32_t *pairs, uint64_t cap, Workspace &ws,

@@ -44,7 +44,13 @@ def check_single(f_np, t):
     assert np.array_equal(W.cpu().numpy().view(np.uint64), W_ref), f"triplets {f_np.shape}"
     assert k == len(p_ref) and root == int(roots[0])
     assert np.array_equal(pairs[:k].cpu().numpy().view(np.uint32), p_ref), f"pairs {f_np.shape}"
-    assert np.array_equal(lab.cpu().numpy().view(np.uint32), oracle.components(f_np, t)), f"labels {f_np.shape}"
+    lab_ref = oracle.components(f_np, t)
+    assert np.array_equal(lab.cpu().numpy().view(np.uint32), lab_ref), f"labels {f_np.shape}"
+    # the labels taken inside the repair pass (its full-table paths included)
+    mt.mt_build_components(f, W, t, lab, ws)
+    mt.mt_sync_status(ws)
+    assert np.array_equal(W.cpu().numpy().view(np.uint64), W_ref), f"fused triplets {f_np.shape}"
+    assert np.array_equal(lab.cpu().numpy().view(np.uint32), lab_ref), f"fused labels {f_np.shape}"
 
 
 def check_wide(f_np, t):
