@@ -742,6 +742,28 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
 // global walk for a target without a copy. Concurrent repairs move entries
 // along their own chains below their own saddles, which keeps every walk's
 // end.
+// The label at t of the component reached from x: the end r of the walk
+// along links with f(s) <= t (Algorithm 4 with a value test), or 0xFFFFFFFF
+// when eps > 0 and r heads a branch of persistence below eps (its component
+// lies in a filled pit). Bit 32 of the result is set if the walk ran out of
+// steps. Out of line: the callers take it for a minority of vertices, and
+// inlined copies in their unrolled loops slow the common path.
+__device__ __noinline__ uint64_t label_walk(const uint64_t *W, const Field f, uint32_t x, float t, float eps)
+{
+    for (uint32_t h = 0;; h++) {
+        const uint64_t T = W[x];
+        const uint32_t s = tri_s(T), v = tri_v(T);
+        if ((s == x && v == x) || !(f[s] <= t)) break;
+        x = v;
+        if (h >= kChaseLimit) return (1ull << 32) | x;
+    }
+    if (eps > 0.0f) {
+        const uint32_t s = tri_s(W[x]);
+        if (s != x && !(f[s] - f[x] >= eps)) return 0xFFFFFFFFull;
+    }
+    return x;
+}
+
 template <int LX, int LY, int LZ>
 struct RepairShape {
     static constexpr uint32_t TV = 1u << (LX + LY + LZ);
@@ -811,29 +833,16 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
     bool ok = true;
     constexpr uint32_t OUT = 0xFFFFFFFFu;  // label of a vertex outside G_t (or in a filled pit)
     const float lt = la.t;
-    // representative at t: the walk along links with f(s) <= t
-    auto rep_at_t = [&](uint32_t x) -> uint32_t {
-        for (uint32_t h = 0;; h++) {
-            const uint64_t T = W[x];
-            const uint32_t s = tri_s(T), v = tri_v(T);
-            if ((s == x && v == x) || !(f[s] <= lt)) return x;
-            x = v;
-            if (h >= kChaseLimit) {
-                ok = false;
-                return x;
-            }
-        }
+    // label at t reached from x: x itself when x is known to head its
+    // component (walk false) and eps <= 0, else label_walk
+    auto label_from = [&](uint32_t x, bool walk) -> uint32_t {
+        if (!walk && !(la.eps > 0.0f)) return x;
+        const uint64_t r = label_walk(W, f, x, lt, la.eps);
+        if (r >> 32) ok = false;
+        return (uint32_t)r;
     };
-    // with eps > 0: 0xFFFFFFFF for a representative heading a branch of
-    // persistence below eps (its component lies in a filled pit)
-    auto simplified = [&](uint32_t r) -> uint32_t {
-        if (!(la.eps > 0.0f)) return r;
-        const uint32_t s = tri_s(W[r]);
-        if (s == r) return r;  // the root
-        return f[s] - f[r] >= la.eps ? r : OUT;
-    };
-    // label of branch minimum m (saddle s) whose link leads to r
-    auto min_label = [&](uint32_t m, float fs, uint32_t r) { return simplified(fs <= lt ? rep_at_t(r) : m); };
+    // label of branch minimum m (saddle value fs) whose link leads to r
+    auto min_label = [&](uint32_t m, float fs, uint32_t r) { return fs <= lt ? label_from(r, true) : label_from(m, false); };
 
     for (uint32_t i = threadIdx.x; i < HS; i += NT) hkey[i] = EMPTY;
     if (threadIdx.x == 0) s_nmin = 0, s_ncopy = 0;
@@ -944,8 +953,7 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
             const uint32_t kt = order_key(lt);
             uint32_t lo = 0;
             while (lo < H && ek[b + lo] <= kt) lo++;
-            const uint32_t r = lo ? ev[b + lo - 1] : x0v;
-            slab[hslot[h]] = simplified(lo == H ? rep_at_t(r) : r);
+            slab[hslot[h]] = label_from(lo ? ev[b + lo - 1] : x0v, lo == H);
         }
     }
     __syncthreads();
@@ -1000,7 +1008,7 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
             }
             if (r != t) st_tri(W + u, tri_pack(u, r));
             // t >= f(u): the walk at t passes the representative at u
-            if (LAB) la.labels[u] = !(fb[k] <= lt) ? OUT : c != NOSLOT ? slab[c] : simplified(rep_at_t(r));
+            if (LAB) la.labels[u] = !(fb[k] <= lt) ? OUT : c != NOSLOT ? slab[c] : label_from(r, true);
         }
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
