@@ -764,6 +764,16 @@ __device__ __noinline__ uint64_t label_walk(const uint64_t *W, const Field f, ui
     return x;
 }
 
+// Representative(x, u) for an inner vertex whose target's copy does not reach
+// its level (Algorithm 4 along the global chain); bit 32 set if the walk ran
+// out of steps. Out of line for the same reason as label_walk.
+__device__ __noinline__ uint64_t repair_walk(const uint64_t *W, const Field f, uint32_t x, uint32_t u, float fu)
+{
+    uint32_t steps = 0;
+    const uint32_t r = representative_cached(W, f, x, u, fu, steps);
+    return steps > kChaseLimit ? (1ull << 32) | r : r;
+}
+
 template <int LX, int LY, int LZ>
 struct RepairShape {
     static constexpr uint32_t TV = 1u << (LX + LY + LZ);
@@ -999,12 +1009,12 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
                 global = lo == H;
             }
             if (global) {
-                uint32_t steps = 0;
-                r = representative_cached(W, f, r, u, fb[k], steps);
-                if (steps > kChaseLimit) {
+                const uint64_t rr = repair_walk(W, f, r, u, fb[k]);
+                if (rr >> 32) {
                     ok = false;
                     continue;
                 }
+                r = (uint32_t)rr;
             }
             if (r != t) st_tri(W + u, tri_pack(u, r));
             // t >= f(u): the walk at t passes the representative at u
