@@ -631,6 +631,8 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
     static_assert(FH <= kCrossHash / 3 * 2, "hash load factor");
     constexpr unsigned long long EMPTY = ~0ull;
     __shared__ unsigned long long hkey[kCrossHash], hval[kCrossHash];
+    __shared__ uint16_t todo[kCrossHash];  // the occupied slots, compacted
+    __shared__ uint32_t s_ntodo;
     uint32_t tile;
     const FieldDesc fd = loc.tile(blockIdx.x, tile);
     uint64_t *W = fd.W;
@@ -646,6 +648,7 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
     const uint32_t *fby = fd.faces + (size_t)(tile + ntx) * (2 * FH) + FH + FX;
     const uint32_t *fbz = fd.faces + (size_t)(tile + ntx * nty) * (2 * FH) + FH + FX + FY;
     for (uint32_t i = threadIdx.x; i < kCrossHash; i += blockDim.x) hkey[i] = EMPTY, hval[i] = EMPTY;
+    if (threadIdx.x == 0) s_ntodo = 0;
     __syncthreads();
     const bool hx = x0 + TX < nx, hy = y0 + TY < ny, hz = z0 + TZ < nz;
     for (uint32_t e = threadIdx.x; e < FH; e += blockDim.x) {
@@ -690,10 +693,24 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
         }
     }
     __syncthreads();
+    // list the occupied slots (one shared atomic per warp and pass), so that
+    // the merges spread over all threads instead of one thread per fixed
+    // group of slots, most of them empty
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t i0 = 0; i0 < kCrossHash; i0 += blockDim.x) {
+        const uint32_t i = i0 + threadIdx.x;
+        const bool full = i < kCrossHash && hkey[i] != EMPTY;
+        const uint32_t bal = __ballot_sync(0xffffffffu, full);
+        uint32_t pos = 0;
+        if (lane == 0 && bal) pos = atomicAdd(&s_ntodo, __popc(bal));
+        pos = __shfl_sync(0xffffffffu, pos, 0) + __popc(bal & ((1u << lane) - 1u));
+        if (full) todo[pos] = (uint16_t)i;
+    }
+    __syncthreads();
     bool ok = true;
-    for (uint32_t i = threadIdx.x; i < kCrossHash; i += blockDim.x) {
+    for (uint32_t j = threadIdx.x; j < s_ntodo; j += blockDim.x) {
+        const uint32_t i = todo[j];
         const unsigned long long key = hkey[i];
-        if (key == EMPTY) continue;
         ok &= merge(W, f, (uint32_t)hval[i], (uint32_t)(key >> 32), (uint32_t)key);
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
