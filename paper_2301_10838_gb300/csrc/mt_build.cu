@@ -798,8 +798,8 @@ struct RepairShape {
     static constexpr uint32_t kCap = TV / 16 / kRepairShrink;   // copies
     static constexpr uint32_t kHash = TV / 8 / kRepairShrink;   // hash slots for targets
     static constexpr uint32_t kList = TV / 4 / kRepairShrink;   // branch minima listed
-    static constexpr size_t kSmem =
-        (size_t)kCap * kHops * 12 + (size_t)kHash * 4 + (size_t)kHash * 2 + (size_t)kList * 2;
+    static constexpr size_t kSmem = (size_t)kCap * kHops * 12 + (size_t)kHash * 4 + (size_t)kHash * 2 +
+                                    (size_t)kList * 2 + (size_t)kCap * 2;
     static constexpr size_t kSmemLab = kSmem + (size_t)kCap * 4;  // + each copy's label
 };
 
@@ -825,6 +825,7 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
     uint32_t *slab = hkey + HS;                // LAB: label at t of each copy's target
     uint16_t *hslot = reinterpret_cast<uint16_t *>(slab + (LAB ? CAP : 0));  // copy slots of the targets
     uint16_t *list = hslot + HS;               // branch minima (tile-local ids)
+    uint16_t *cslot = list + LIST;             // hash slot of each copy's target
     __shared__ uint32_t s_nmin, s_ncopy;
 
     uint32_t tile;
@@ -925,13 +926,14 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
         if (hkey[i] == EMPTY) continue;
         const uint32_t c = atomicAdd(&s_ncopy, 1u);
         hslot[i] = c < CAP ? (uint16_t)c : NOSLOT;
+        if (c < CAP) cslot[c] = (uint16_t)i;
     }
     __syncthreads();
 
     // 3. branch minima (items below nmin) and copies of target chains (one
-    //    item per hash slot)
-    const uint32_t nmin = min(s_nmin, LIST);
-    for (uint32_t i = threadIdx.x; i < nmin + HS; i += NT) {
+    //    item per copy: copy c serves the target in hash slot cslot[c])
+    const uint32_t nmin = min(s_nmin, LIST), ncopy = min(s_ncopy, CAP);
+    for (uint32_t i = threadIdx.x; i < nmin + ncopy; i += NT) {
         if (i < nmin) {
             const uint32_t u = gid_of(list[i]);
             const uint64_t T = W[u];
@@ -944,10 +946,9 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
             if (LAB) la.labels[u] = min_label(u, fs, r);  // 0xFFFFFFFF above t: step 4
             continue;
         }
-        const uint32_t h = i - nmin;
-        const uint32_t x0v = hkey[h];
-        if (x0v == EMPTY || hslot[h] == NOSLOT) continue;
-        const uint32_t b = (uint32_t)hslot[h] * H;
+        const uint32_t c = i - nmin;  // copy c, of the target in hash slot cslot[c]
+        const uint32_t x0v = hkey[cslot[c]];
+        const uint32_t b = c * H;
         uint32_t x = x0v, j = 0;
         bool ended = false;
         uint64_t T = W[x];
@@ -980,7 +981,7 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
             const uint32_t kt = order_key(lt);
             uint32_t lo = 0;
             while (lo < H && ek[b + lo] <= kt) lo++;
-            slab[hslot[h]] = label_from(lo ? ev[b + lo - 1] : x0v, lo == H);
+            slab[c] = label_from(lo ? ev[b + lo - 1] : x0v, lo == H);
         }
     }
     __syncthreads();
