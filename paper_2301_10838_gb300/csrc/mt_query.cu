@@ -341,10 +341,40 @@ __global__ void __launch_bounds__(kLabThreads, 4) k_labels(const Field f, const 
     }
     __syncthreads();
 
-    // 2. one chase per hashed start
-    for (uint32_t i = threadIdx.x; i < HS; i += NT) {
-        const uint32_t st = hkey[i];
-        if (st != EMPTY) hval[i] = simplified(chase(st));
+    // 2. one chase per hashed start. Each warp takes the occupied slots of
+    //    its own HS / warps slots and deals them out to its lanes in order
+    //    (ballot masks in registers), so that every lane has a chase instead
+    //    of one lane per fixed group of mostly empty slots.
+    constexpr uint32_t PER = HS / (NT / 32);  // slots per warp
+    if constexpr (PER >= 32 && PER % 32 == 0) {
+        constexpr uint32_t G = PER >= 32 ? PER / 32 : 1;  // (1 only in the branch not taken)
+        const uint32_t lane = threadIdx.x & 31, wbase = (threadIdx.x >> 5) * PER;
+        uint32_t mask[G], tot = 0;
+#pragma unroll
+        for (uint32_t g = 0; g < G; g++) {
+            mask[g] = __ballot_sync(0xffffffffu, hkey[wbase + g * 32 + lane] != EMPTY);
+            tot += __popc(mask[g]);
+        }
+        for (uint32_t r = lane; r < tot; r += 32) {
+            // the slot of rank r among the warp's occupied slots
+            uint32_t rr = r, i = 0;
+#pragma unroll
+            for (uint32_t g = 0; g < G; g++) {
+                const uint32_t c = __popc(mask[g]);
+                if (rr < c && i == 0) {
+                    uint32_t m = mask[g];
+                    for (uint32_t k = 0; k < rr; k++) m &= m - 1;
+                    i = wbase + g * 32 + __ffs(m);  // 1 + the slot
+                }
+                rr = rr < c ? rr : rr - c;
+            }
+            hval[i - 1] = simplified(chase(hkey[i - 1]));
+        }
+    } else {
+        for (uint32_t i = threadIdx.x; i < HS; i += NT) {
+            const uint32_t st = hkey[i];
+            if (st != EMPTY) hval[i] = simplified(chase(st));
+        }
     }
     __syncthreads();
 
