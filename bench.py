@@ -155,22 +155,37 @@ def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 32), fused: bool
             "cross_edges": C}
 
 
+def kernel_source_digest(kernel: str) -> str:
+    """sha256 (16 hex digits) of the source a kernel's counters depend on:
+    its section of mt_build.cu (from its "// ---- name" marker line to the
+    next marker) and the shared device header. Edits elsewhere in the file
+    leave it unchanged."""
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_2301_10838_gb300", "csrc")
+    with open(os.path.join(csrc, "mt_build.cu")) as fh:
+        lines = fh.read().splitlines(keepends=True)
+    marks = [i for i, ln in enumerate(lines) if ln.startswith("// ----")]
+    start = next(i for i in marks if lines[i].rstrip().endswith(" " + kernel))
+    end = next((i for i in marks if i > start), len(lines))
+    h = hashlib.sha256("".join(lines[start:end]).encode())
+    with open(os.path.join(csrc, "mt_device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(kernel: str) -> dict:
     """The committed ncu record of `kernel` at the benchmark workload: DRAM
     bytes per launch and what the profile shows the kernel is limited by.
-    Empty if there is none or the kernel source changed since it was taken."""
-    import hashlib
-
+    Empty if there is none or the kernel's source changed since it was taken."""
     prof = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{WORKLOAD}.json")
-    src = os.path.join(ROOT, "paper_2301_10838_gb300", "csrc", "mt_build.cu")
     try:
         with open(prof) as fh:
             rec = json.load(fh)
-        with open(src, "rb") as fh:
-            h = hashlib.sha256(fh.read()).hexdigest()[:16]
-    except (OSError, ValueError):
+        h = kernel_source_digest(rec.get("source_section", "k_" + kernel))
+    except (OSError, ValueError, StopIteration):
         return {}
-    return rec if rec.get("mt_build_cu_sha256_16") == h else {}
+    return rec if rec.get("source_sha256_16") == h else {}
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
