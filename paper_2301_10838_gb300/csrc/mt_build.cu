@@ -743,8 +743,9 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
 //     it does the walk go on along the global chain.
 // Steps 1 and 4 load four rows per thread before using any, so that the
 // loads of a thread overlap. A branch minimum that finds the list full is
-// repaired on the spot in step 1; a target without a slot (hash or copies
-// full) is chased along the global chain in step 4.
+// marked in a bitmap in step 1 and repaired in step 3 (kept out of the
+// unrolled row loop); a target without a slot (hash or copies full) is
+// chased along the global chain in step 4.
 //
 // With LAB the pass also labels the components of G_t (the labels of
 // k_labels) where it already stands. The representative of u at level t is
@@ -799,7 +800,7 @@ struct RepairShape {
     static constexpr uint32_t kHash = TV / 8 / kRepairShrink;   // hash slots for targets
     static constexpr uint32_t kList = TV / 4 / kRepairShrink;   // branch minima listed
     static constexpr size_t kSmem = (size_t)kCap * kHops * 12 + (size_t)kHash * 4 + (size_t)kHash * 2 +
-                                    (size_t)kList * 2 + (size_t)kCap * 2;
+                                    (size_t)kList * 2 + (size_t)kCap * 2 + (size_t)TV / 8;
     static constexpr size_t kSmemLab = kSmem + (size_t)kCap * 4;  // + each copy's label
 };
 
@@ -813,6 +814,7 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
     constexpr uint32_t NB = 4;  // rows loaded together
     static_assert(TV % (NT * NB) == 0, "whole batches of rows");
     static_assert((H & (H - 1)) == 0 && (HS & (HS - 1)) == 0, "powers of two");
+    static_assert((HS + LIST + CAP) % 2 == 0, "the bitmap after the 16-bit arrays is 4-byte aligned");
     constexpr uint32_t EMPTY = 0xFFFFFFFFu;  // free hash slot (not a vertex id: ids are < n < 2^32 - 1)
     constexpr uint32_t END = 0xFFFFFFFFu;    // copied saddle after the chain's root: above every (key, id)
     constexpr uint16_t NOSLOT = 0xFFFFu;
@@ -826,6 +828,7 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
     uint16_t *hslot = reinterpret_cast<uint16_t *>(slab + (LAB ? CAP : 0));  // copy slots of the targets
     uint16_t *list = hslot + HS;               // branch minima (tile-local ids)
     uint16_t *cslot = list + LIST;             // hash slot of each copy's target
+    uint32_t *ovf = reinterpret_cast<uint32_t *>(cslot + CAP);  // bit per vertex: minima past the list
     __shared__ uint32_t s_nmin, s_ncopy;
 
     uint32_t tile;
@@ -873,6 +876,7 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
     auto min_label = [&](uint32_t m, float fs, uint32_t r) { return fs <= lt ? label_from(r, true) : label_from(m, false); };
 
     for (uint32_t i = threadIdx.x; i < HS; i += NT) hkey[i] = EMPTY;
+    for (uint32_t i = threadIdx.x; i < TV / 32; i += NT) ovf[i] = 0;
     if (threadIdx.x == 0) s_nmin = 0, s_ncopy = 0;
     __syncthreads();
 
@@ -908,13 +912,8 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
                 pos = __shfl_sync(0xffffffffu, pos, 0) + __popc(bal & ((1u << lane) - 1u));
                 if (is_min && pos < LIST) {
                     list[pos] = (uint16_t)l;
-                } else if (is_min) {  // list full: repair this branch minimum now
-                    uint32_t steps = 0;
-                    const float fs = f[s];
-                    const uint32_t r = representative_cached(W, f, v, s, fs, steps);
-                    if (steps > kChaseLimit) ok = false;
-                    else if (r != v) st_tri(W + u, tri_pack(s, r));
-                    if (LAB) la.labels[u] = min_label(u, fs, r);
+                } else if (is_min) {  // list full: mark it for step 3
+                    atomicOr(&ovf[l >> 5], 1u << (l & 31));
                 }
             }
         }
@@ -932,18 +931,26 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
 
     // 3. branch minima (items below nmin) and copies of target chains (one
     //    item per copy: copy c serves the target in hash slot cslot[c])
+    // Repair of the branch minimum with local id l (and with LAB its label,
+    // which step 4 overwrites with 0xFFFFFFFF above t)
+    auto repair_min = [&](uint32_t l) {
+        const uint32_t u = gid_of(l);
+        const uint64_t T = W[u];
+        const uint32_t s = tri_s(T), t = tri_v(T);
+        uint32_t steps = 0;
+        const float fs = f[s];
+        const uint32_t r = representative_cached(W, f, t, s, fs, steps);
+        if (steps > kChaseLimit) ok = false;
+        else if (r != t) st_tri(W + u, tri_pack(s, r));
+        if (LAB) la.labels[u] = min_label(u, fs, r);
+    };
     const uint32_t nmin = min(s_nmin, LIST), ncopy = min(s_ncopy, CAP);
+    if (s_nmin > LIST)  // the minima that found the list full
+        for (uint32_t w = threadIdx.x; w < TV / 32; w += NT)
+            for (uint32_t m = ovf[w]; m; m &= m - 1) repair_min(w * 32 + __ffs(m) - 1);
     for (uint32_t i = threadIdx.x; i < nmin + ncopy; i += NT) {
         if (i < nmin) {
-            const uint32_t u = gid_of(list[i]);
-            const uint64_t T = W[u];
-            const uint32_t s = tri_s(T), t = tri_v(T);
-            uint32_t steps = 0;
-            const float fs = f[s];
-            const uint32_t r = representative_cached(W, f, t, s, fs, steps);
-            if (steps > kChaseLimit) ok = false;
-            else if (r != t) st_tri(W + u, tri_pack(s, r));
-            if (LAB) la.labels[u] = min_label(u, fs, r);  // 0xFFFFFFFF above t: step 4
+            repair_min(list[i]);
             continue;
         }
         const uint32_t c = i - nmin;  // copy c, of the target in hash slot cslot[c]

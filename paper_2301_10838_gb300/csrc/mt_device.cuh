@@ -18,8 +18,8 @@ enum : uint32_t {
 };
 
 // Table sizes of the shared-memory hashes and lists. Each table has a path
-// for when it is full (merge in place, repair on the spot, chase the global
-// chain); the defaults keep those paths rare. A library built with
+// for when it is full (merge in place, repair from an overflow bitmap, chase
+// the global chain); the defaults keep those paths rare. A library built with
 // MT_STRESS_TABLES shrinks the tables so that the tests reach every such
 // path; its results are the same.
 #ifdef MT_STRESS_TABLES

@@ -2,7 +2,7 @@
 
 The defaults size the kernels' tables so that these paths are rare: k_tile
 merges an edge in place when its hash is crowded, k_repair repairs a branch
-minimum on the spot when its list is full and chases a target without a copy
+minimum from an overflow bitmap when its list is full and chases a target without a copy
 slot along the global chain, k_labels lets a vertex whose chain start found
 no slot chase the chain itself. A library built with MT_STRESS_TABLES
 shrinks those tables (and nothing else); stress_cases.py runs the parity
