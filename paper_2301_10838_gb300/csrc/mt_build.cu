@@ -944,13 +944,17 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
         else if (r != t) st_tri(W + u, tri_pack(s, r));
         if (LAB) la.labels[u] = min_label(u, fs, r);
     };
+    // items: the listed minima, the copies, then (when the list overflowed)
+    // the words of the bitmap of the minima past it; the two kinds of minima
+    // share one call of repair_min, so that its code appears once
     const uint32_t nmin = min(s_nmin, LIST), ncopy = min(s_ncopy, CAP);
-    if (s_nmin > LIST)  // the minima that found the list full
-        for (uint32_t w = threadIdx.x; w < TV / 32; w += NT)
-            for (uint32_t m = ovf[w]; m; m &= m - 1) repair_min(w * 32 + __ffs(m) - 1);
-    for (uint32_t i = threadIdx.x; i < nmin + ncopy; i += NT) {
-        if (i < nmin) {
-            repair_min(list[i]);
+    const uint32_t nover = s_nmin > LIST ? TV / 32 : 0;
+    for (uint32_t i = threadIdx.x; i < nmin + ncopy + nover; i += NT) {
+        if (i < nmin || i >= nmin + ncopy) {
+            const bool listed = i < nmin;
+            const uint32_t w = i - nmin - ncopy;
+            for (uint32_t m = listed ? 1u : ovf[w]; m; m &= m - 1)
+                repair_min(listed ? (uint32_t)list[i] : w * 32 + __ffs(m) - 1);
             continue;
         }
         const uint32_t c = i - nmin;  // copy c, of the target in hash slot cslot[c]
