@@ -619,19 +619,30 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 2 : 1536 / NT) k_tile(Loc loc
 // earlier is merged, so the CTA keeps, per pair of tops, only the edge with
 // the earliest level (a shared-memory hash with 64-bit atomicMin on
 // (key, id) of S) and merges that one, starting its climbs at the tops.
-constexpr uint32_t kCrossHash = 2048;
+//
+// Pairs from different faces never coincide (their second tops lie in
+// different neighbour tiles), so the three faces go through one small hash
+// in turn: fill it with the face's edges, then each edge that still holds
+// its slot's minimum (S identifies an edge within a face) lists itself and
+// clears the slot. The merges then run from the list, one per thread, all
+// lanes busy; the small footprint lets 8 CTAs share an SM.
+constexpr uint32_t kCrossHash = 1024;
 
 template <int LX, int LY, int LZ, class Loc>
-__global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
+__global__ void __launch_bounds__(256, 8) k_cross(Loc loc, uint32_t *status)
 {
     if (block_skips(status)) return;
     using TS = Tile<LX, LY, LZ>;
     constexpr uint32_t TX = TS::TX, TY = TS::TY, TZ = TS::TZ;
     constexpr uint32_t FX = TY * TZ, FY = TX * TZ, FZ = TX * TY, FH = FX + FY + FZ;
-    static_assert(FH <= kCrossHash / 3 * 2, "hash load factor");
+    constexpr uint32_t FMAX = FX > FY ? (FX > FZ ? FX : FZ) : (FY > FZ ? FY : FZ);
+    constexpr uint32_t PER = (FMAX + 255) / 256;  // edges of one face per thread
+    static_assert(FMAX <= kCrossHash / 3 * 2, "hash load factor");
+    static_assert(FH <= 65536, "16-bit face edge indices");
     constexpr unsigned long long EMPTY = ~0ull;
     __shared__ unsigned long long hkey[kCrossHash], hval[kCrossHash];
-    __shared__ uint16_t todo[kCrossHash];  // the occupied slots, compacted
+    __shared__ uint32_t todo_s[FH];  // the saddle S of each edge to merge
+    __shared__ uint16_t todo_e[FH];  // and its face edge index
     __shared__ uint32_t s_ntodo;
     uint32_t tile;
     const FieldDesc fd = loc.tile(blockIdx.x, tile);
@@ -647,71 +658,81 @@ __global__ void __launch_bounds__(256) k_cross(Loc loc, uint32_t *status)
     const uint32_t *fbx = fd.faces + (size_t)(tile + 1) * (2 * FH) + FH;
     const uint32_t *fby = fd.faces + (size_t)(tile + ntx) * (2 * FH) + FH + FX;
     const uint32_t *fbz = fd.faces + (size_t)(tile + ntx * nty) * (2 * FH) + FH + FX + FY;
-    for (uint32_t i = threadIdx.x; i < kCrossHash; i += blockDim.x) hkey[i] = EMPTY, hval[i] = EMPTY;
-    if (threadIdx.x == 0) s_ntodo = 0;
-    __syncthreads();
     const bool hx = x0 + TX < nx, hy = y0 + TY < ny, hz = z0 + TZ < nz;
-    for (uint32_t e = threadIdx.x; e < FH; e += blockDim.x) {
-        uint32_t a, b, ta, tb;
+    // edge e of the +x, +y, +z faces: its ends (a in this tile, b in the
+    // neighbour) and their tops; false where the edge does not exist
+    auto edge = [&](uint32_t e, uint32_t &a, uint32_t &b, uint32_t &ta, uint32_t &tb) -> bool {
         if (e < FX) {
             const uint32_t ly = e % TY, lz = e / TY;
-            if (!hx || ly >= wy || lz >= wz) continue;
+            if (!hx || ly >= wy || lz >= wz) return false;
             a = base + lz * nxy + ly * nx + (TX - 1);
             b = a + 1;
-            ta = fa[e];
             tb = fbx[e];
         } else if (e < FX + FY) {
             const uint32_t k = e - FX, lx = k % TX, lz = k / TX;
-            if (!hy || lx >= wx || lz >= wz) continue;
+            if (!hy || lx >= wx || lz >= wz) return false;
             a = base + lz * nxy + (TY - 1) * nx + lx;
             b = a + nx;
-            ta = fa[e];
             tb = fby[k];
         } else {
             const uint32_t k = e - FX - FY, lx = k % TX, ly = k / TX;
-            if (!hz || lx >= wx || ly >= wy) continue;
+            if (!hz || lx >= wx || ly >= wy) return false;
             a = base + (TZ - 1) * nxy + ly * nx + lx;
             b = a + nxy;
-            ta = fa[e];
             tb = fbz[k];
         }
-        const float va = f[a], vb = f[b];
-        const uint32_t S = before(vb, b, va, a) ? a : b;
-        const float vS = S == a ? va : vb;
-        const unsigned long long key = ((unsigned long long)ta << 32) | tb;
-        const uint32_t bits = vS == 0.0f ? 0u : __float_as_uint(vS);
-        const uint32_t kS = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
-        const unsigned long long val = ((unsigned long long)kS << 32) | S;
-        uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 53) & (kCrossHash - 1);
-        for (uint32_t p = 0; p < kCrossHash; p++) {
-            const unsigned long long k0 = atomicCAS(&hkey[h], EMPTY, key);
-            if (k0 == EMPTY || k0 == key) {
-                atomicMin(&hval[h], val);
-                break;
+        ta = fa[e];
+        return true;
+    };
+    for (uint32_t i = threadIdx.x; i < kCrossHash; i += blockDim.x) hkey[i] = EMPTY, hval[i] = EMPTY;
+    if (threadIdx.x == 0) s_ntodo = 0;
+    __syncthreads();
+    for (uint32_t face = 0; face < 3; face++) {
+        const uint32_t e0 = face == 0 ? 0 : face == 1 ? FX : FX + FY;
+        const uint32_t e1 = face == 0 ? FX : face == 1 ? FX + FY : FH;
+        uint32_t slot[PER];
+        unsigned long long mine[PER];
+#pragma unroll
+        for (uint32_t q = 0; q < PER; q++) {
+            const uint32_t e = e0 + q * 256 + threadIdx.x;
+            mine[q] = EMPTY;
+            uint32_t a, b, ta, tb;
+            if (e >= e1 || !edge(e, a, b, ta, tb)) continue;
+            const float va = f[a], vb = f[b];
+            const uint32_t S = before(vb, b, va, a) ? a : b;
+            const float vS = S == a ? va : vb;
+            const unsigned long long key = ((unsigned long long)ta << 32) | tb;
+            const uint32_t bits = vS == 0.0f ? 0u : __float_as_uint(vS);
+            const uint32_t kS = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+            mine[q] = ((unsigned long long)kS << 32) | S;
+            uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 54) & (kCrossHash - 1);
+            for (uint32_t p = 0; p < kCrossHash; p++) {
+                const unsigned long long k0 = atomicCAS(&hkey[h], EMPTY, key);
+                if (k0 == EMPTY || k0 == key) {
+                    atomicMin(&hval[h], mine[q]);
+                    break;
+                }
+                h = (h + 1) & (kCrossHash - 1);
             }
-            h = (h + 1) & (kCrossHash - 1);
+            slot[q] = h;
         }
+        __syncthreads();
+        // the winner of each slot lists its edge and clears the slot
+#pragma unroll
+        for (uint32_t q = 0; q < PER; q++) {
+            if (mine[q] == EMPTY || hval[slot[q]] != mine[q]) continue;
+            const uint32_t j = atomicAdd(&s_ntodo, 1u);
+            todo_s[j] = (uint32_t)mine[q];
+            todo_e[j] = (uint16_t)(e0 + q * 256 + threadIdx.x);
+            hkey[slot[q]] = EMPTY, hval[slot[q]] = EMPTY;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    // list the occupied slots (one shared atomic per warp and pass), so that
-    // the merges spread over all threads instead of one thread per fixed
-    // group of slots, most of them empty
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint32_t i0 = 0; i0 < kCrossHash; i0 += blockDim.x) {
-        const uint32_t i = i0 + threadIdx.x;
-        const bool full = i < kCrossHash && hkey[i] != EMPTY;
-        const uint32_t bal = __ballot_sync(0xffffffffu, full);
-        uint32_t pos = 0;
-        if (lane == 0 && bal) pos = atomicAdd(&s_ntodo, __popc(bal));
-        pos = __shfl_sync(0xffffffffu, pos, 0) + __popc(bal & ((1u << lane) - 1u));
-        if (full) todo[pos] = (uint16_t)i;
-    }
-    __syncthreads();
     bool ok = true;
     for (uint32_t j = threadIdx.x; j < s_ntodo; j += blockDim.x) {
-        const uint32_t i = todo[j];
-        const unsigned long long key = hkey[i];
-        ok &= merge(W, f, (uint32_t)hval[i], (uint32_t)(key >> 32), (uint32_t)key);
+        uint32_t a, b, ta, tb;
+        edge(todo_e[j], a, b, ta, tb);
+        ok &= merge(W, f, todo_s[j], ta, tb);
     }
     if (!ok) raise_status(status, ST_TIMEOUT);
 }
