@@ -84,38 +84,51 @@ __global__ void __launch_bounds__(kCompactThreads) k_pairs_count(Loc loc, uint32
 
 // Exclusive scan of one field's chunk counts in place (one CTA of 1024
 // threads per field); the field's total goes to its meta[0] and, in a batch,
-// to npairs[field].
+// to npairs[field]. Warp w owns a contiguous range of chunks and reads it in
+// coalesced rows of 32: a first pass sums the range, one warp scans the 32
+// sums, and a second pass scans each row with shuffles on top of the carry.
 template <class Loc>
 __global__ void __launch_bounds__(1024) k_scan_counts(Loc loc, uint32_t *counts, uint64_t *npairs,
                                                       const uint32_t *status)
 {
     if (block_skips(status)) return;
-    __shared__ uint64_t part[1024];
+    __shared__ uint64_t wsum[32];
     const FieldDesc fd = loc.field(blockIdx.x);
     uint32_t *cnt = counts + fd.chunk0;
     const uint64_t m = (fd.n + kCompactChunk - 1) / kCompactChunk;
-    const uint64_t per = (m + 1023) / 1024;
-    const uint64_t a = threadIdx.x * per, b = a + per < m ? a + per : m;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t per = ((m + 31) / 32 + 31) / 32 * 32;  // chunks per warp, whole rows
+    const uint64_t a = warp * per, b = a + per < m ? a + per : m;
     uint64_t s = 0;
-    for (uint64_t i = a; i < b; i++) s += cnt[i];
-    part[threadIdx.x] = s;
+    for (uint64_t i = a + lane; i < b; i += 32) s += cnt[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) wsum[warp] = s;
     __syncthreads();
-    // Hillis-Steele inclusive scan of the 1024 partial sums
-    for (int o = 1; o < 1024; o <<= 1) {
-        const uint64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (warp == 0) {
+        const uint64_t v = wsum[lane];
+        uint64_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        wsum[lane] = incl - v;  // exclusive
+        if (lane == 31) {
+            fd.meta[0] = incl;
+            if (npairs) npairs[blockIdx.x] = incl;
+        }
     }
-    uint64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-    for (uint64_t i = a; i < b; i++) {
-        const uint32_t c = cnt[i];
-        cnt[i] = (uint32_t)run;
-        run += c;
-    }
-    if (threadIdx.x == 1023) {
-        fd.meta[0] = part[1023];
-        if (npairs) npairs[blockIdx.x] = part[1023];
+    __syncthreads();
+    uint64_t carry = wsum[warp];
+    for (uint64_t r = a; r < b; r += 32) {
+        const uint64_t i = r + lane;
+        const uint32_t c = i < b ? cnt[i] : 0u;
+        uint32_t incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (i < b) cnt[i] = (uint32_t)(carry + incl - c);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
 }
 
