@@ -4,11 +4,11 @@
 
 One step is one pass of the whole hot path over the 1024^3 lognormal field
 exp(0.8 g) (g a Gaussian random field with P(k) ~ k^-2, float32, seed 1+rank):
-  mt_build_components   (validate, init, descent jumping, merge, repair with
+  mt_build_step         (validate, init, descent jumping, merge, repair with
                          the labels of G_t at the field's median value taken
-                         inside the repair pass; the launch configuration the
-                         autotuner picks)
-  mt_persistence_pairs  (ordered pair compaction; synchronises)
+                         inside the repair pass, then the ordered pair
+                         compaction; the launch configuration the autotuner
+                         picks; synchronises)
 --separate times the same work as three calls (mt_build_triplets_cfg,
 mt_persistence_pairs, mt_components_at); either way the line reports the
 other form too ("other_step_form").
@@ -268,8 +268,9 @@ def run_ours(args):
     pairs = torch.empty((npairs, 2), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    # one step: the build with the labels of G_t taken inside its repair pass,
-    # then the pairs (--separate: build, pairs and labels as three calls)
+    # one step: mt_build_step, the build with the labels of G_t taken inside
+    # its repair pass, then the pairs (--separate: build, pairs and labels as
+    # three calls)
     fused = not args.separate
 
     def step_separate():
@@ -279,8 +280,7 @@ def run_ours(args):
         return np_
 
     def step_fused():
-        mt.mt_build_components(f, W, t_thr, labels, ws, cfg=cfg)
-        np_, root = mt.mt_persistence_pairs(f, W, pairs, ws)
+        np_, root = mt.mt_build_step(f, W, t_thr, labels, pairs, ws, cfg=cfg)
         return np_
 
     step = step_fused if fused else step_separate
@@ -333,7 +333,7 @@ def run_ours(args):
     mt.mt_sync_status(ws)
     other_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
     other_step = {"step": "mt_build_triplets_cfg + mt_persistence_pairs + mt_components_at" if fused
-                  else "mt_build_components + mt_persistence_pairs",
+                  else "mt_build_step",
                   "ms_per_step": round(other_ms, 3),
                   "phases_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in other_phases.items()}}
 
@@ -467,8 +467,8 @@ def run_ours(args):
                 "grid": [shape[2], shape[1], shape[0]],
                 "field": "exp(0.8 g), g unit-variance GRF P(k)~k^-2, float32, seed 1+rank",
                 "field_sha256": field_sha,
-                "step": ("mt_build_components(tuned cfg, median: labels inside the repair pass) + "
-                         "mt_persistence_pairs") if fused else
+                "step": ("mt_build_step(tuned cfg, median: labels inside the repair pass, "
+                         "then the pairs)") if fused else
                         "mt_build_triplets_cfg(tuned cfg) + mt_persistence_pairs + mt_components_at(median)",
                 "build_cfg": cfg,
                 "threshold": t_thr,
@@ -529,7 +529,7 @@ def _events_ms(fn, reps: int, dev, flush=None) -> list[float]:
 
 def bench_config(name: str, dev, peak: float) -> dict:
     """One of the smaller configs (64^3 white noise, 256^3 quantised GRF):
-    the same step as the benchmark (build with labels at the median + pairs),
+    the same step as the benchmark (mt_build_step, labels at the median),
     L2 flushed (a 256 MiB write) before each step, median of 9 steps."""
     import numpy as np
     import torch
@@ -550,8 +550,7 @@ def bench_config(name: str, dev, peak: float) -> dict:
     cfg, tune_ms = autotune.tune_single(f, W, ws, use_cache=False)
 
     def step():
-        mt.mt_build_components(f, W, t, labels, ws, cfg=cfg)
-        state["k"], _ = mt.mt_persistence_pairs(f, W, pairs, ws)
+        state["k"], _ = mt.mt_build_step(f, W, t, labels, pairs, ws, cfg=cfg)
 
     for _ in range(3):
         step()

@@ -189,6 +189,21 @@ mt_status mt_build_components(const float *d_f, mt_grid g, uint64_t *d_W, float 
                               uint32_t cfg, uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
+ * The whole path in one call: the triplets and labels of mt_build_components
+ * and the pairs of mt_simplified_pairs(d_f, d_W, g, eps, flags, ...) (eps <=
+ * 0: those of mt_persistence_pairs), bit for bit, the pairs taken by the
+ * same ordered compaction. Arguments as mt_build_components plus the pair
+ * outputs of mt_persistence_pairs (d_pairs uint32[cap][2], h_npairs and
+ * h_root on the host; h_root may be NULL). Synchronises `stream`; returns
+ * the workspace status word if it is set, else MT_ERR_CAPACITY (first cap
+ * pairs written, true count in *h_npairs) if the pairs do not fit, else
+ * MT_OK.
+ */
+mt_status mt_build_step(const float *d_f, mt_grid g, uint64_t *d_W, float t, float eps, uint32_t flags, uint32_t cfg,
+                        uint32_t *d_labels, uint32_t *d_pairs, uint64_t cap, uint64_t *h_npairs, uint32_t *h_root,
+                        void *d_ws, size_t ws_bytes, void *stream);
+
+/*
  * Branch decomposition (Section 2.1: every vertex lies on one branch of the
  * tree; the CPU implementation of Section 3.1 keeps each branch's vertices in
  * a list beside its triplets). A minimum u (W[u].s != u, or the root) heads

@@ -38,6 +38,7 @@ __all__ = [
     "mt_build_triplets_cfg",
     "mt_build_autotune",
     "mt_build_components",
+    "mt_build_step",
     "MT_CFG_SMALL_TILES",
     "MT_CFG_FOUR_ROUNDS",
     "MT_CFG_REPAIR_256",
@@ -127,6 +128,8 @@ _SIGS = {
     "mt_build_autotune": ([_P, Grid, _P, _P, ctypes.c_size_t, ctypes.c_uint32, _P, _P, _P], ctypes.c_int32),
     "mt_build_components": ([_P, Grid, _P, ctypes.c_float, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, _P, _P,
                              ctypes.c_size_t, _P], ctypes.c_int32),
+    "mt_build_step": ([_P, Grid, _P, ctypes.c_float, ctypes.c_float, ctypes.c_uint32, ctypes.c_uint32, _P, _P, _U64,
+                       _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int32),
     "mt_components_at_ex": ([_P, _P, Grid, ctypes.c_float, ctypes.c_uint32, _P, _P, ctypes.c_size_t, _P],
                             ctypes.c_int32),
     "mt_persistence_pairs_noalloc": ([_P, _P, Grid, _P, _U64, _P, _P, _P], ctypes.c_int32),
@@ -310,6 +313,29 @@ def mt_build_components(f: torch.Tensor, W: torch.Tensor, t: float, labels: torc
                                       int(flags), int(cfg), _dev(labels, "labels", _I32, n),
                                       _dev(ws, "ws", (torch.uint8,)), ws.numel(), _stream_ptr(stream)),
            "mt_build_components")
+
+
+def mt_build_step(f: torch.Tensor, W: torch.Tensor, t: float, labels: torch.Tensor, pairs: torch.Tensor,
+                  ws: torch.Tensor, eps: float = 0.0, flags: int = 0, cfg: int = 0, stream=None,
+                  allow_partial: bool = False) -> tuple[int, int]:
+    """The whole path in one call: triplets, labels of G_t and the pairs
+    (mt_build_components + mt_simplified_pairs / mt_persistence_pairs);
+    returns (npairs, root). Synchronises the stream."""
+    g = grid_of(f)
+    n = f.numel()
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must have shape (cap, 2)")
+    cap = int(pairs.shape[0])
+    pp = _dev(pairs, "pairs", _I32) if cap else 0
+    npairs = ctypes.c_uint64(0)
+    root = ctypes.c_uint32(0xFFFFFFFF)
+    code = load().mt_build_step(_dev(f, "f", (torch.float32,)), g, _dev(W, "W", _I64, n), float(t), float(eps),
+                                int(flags), int(cfg), _dev(labels, "labels", _I32, n), pp, cap, ctypes.byref(npairs),
+                                ctypes.byref(root), _dev(ws, "ws", (torch.uint8,)), ws.numel(), _stream_ptr(stream))
+    if code == -4 and allow_partial:
+        return int(npairs.value), int(root.value)
+    _check(code, "mt_build_step", f" npairs={npairs.value} cap={cap}")
+    return int(npairs.value), int(root.value)
 
 
 def mt_components_at_ex(f: torch.Tensor, W: torch.Tensor, t: float, flags: int, labels: torch.Tensor,

@@ -189,6 +189,38 @@ mt_status mt_build_components(const float *d_f, mt_grid g, uint64_t *d_W, float 
     return MT_OK;
 }
 
+mt_status mt_build_step(const float *d_f, mt_grid g, uint64_t *d_W, float t, float eps, uint32_t flags, uint32_t cfg,
+                        uint32_t *d_labels, uint32_t *d_pairs, uint64_t cap, uint64_t *h_npairs, uint32_t *h_root,
+                        void *d_ws, size_t ws_bytes, void *stream)
+{
+    if (cfg >= MT_CFG_COUNT || (cfg & MT_CFG_SMALL_TILES)) return MT_ERR_INVALID;
+    uint64_t n;
+    mt_status st = grid_n(g, n);
+    if (st != MT_OK) return st;
+    if (!d_f || !d_W || !d_labels || !h_npairs || std::isnan(t) || std::isnan(eps) || ((uintptr_t)d_f & 3) ||
+        ((uintptr_t)d_W & 7) || ((uintptr_t)d_labels & 3) || (cap && (!d_pairs || ((uintptr_t)d_pairs & 3))) ||
+        (flags & ~MT_SUPERLEVEL))
+        return MT_ERR_INVALID;
+    Workspace ws;
+    if (ws_bytes < build_workspace_bytes(g.nx, g.ny, g.nz) || !carve_workspace(d_ws, ws_bytes, n, ws))
+        return MT_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws.status, 0, 256, s) != cudaSuccess) return MT_ERR_CUDA;
+    const float sg = (flags & MT_SUPERLEVEL) ? -1.0f : 1.0f;
+    const LabelArgs la{d_labels, sg * t, eps};
+    if (launch_build(d_f, d_W, g.nx, g.ny, g.nz, ws, build_faces(d_ws, n), sg, s, cfg, &la) != cudaSuccess)
+        return MT_ERR_CUDA;
+    if (launch_pairs(d_W, n, d_pairs, cap, ws, s, d_f, sg, eps) != cudaSuccess) return MT_ERR_CUDA;
+    uint64_t meta[4];
+    if (readback(ws.meta, ws.status, s, meta) != cudaSuccess) return MT_ERR_CUDA;
+    const uint32_t bits = (uint32_t)meta[3];
+    if (bits) return status_from_bits(bits);
+    *h_npairs = meta[0];
+    if (h_root) *h_root = meta[1] == 1 ? (uint32_t)meta[2] : 0xFFFFFFFFu;
+    if (meta[1] != 1) return MT_ERR_INVALID;  // not a tree of a connected grid
+    return meta[0] > cap ? MT_ERR_CAPACITY : MT_OK;
+}
+
 mt_status mt_build_autotune(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
                             void *stream, float *ms, uint32_t *best)
 {

@@ -286,30 +286,46 @@ __global__ void __launch_bounds__(kWThreads) k_w_pairs_count(const uint64_t *W, 
     if (threadIdx.x == 0) counts[blockIdx.x] = s_cnt;
 }
 
-// exclusive scan of the chunk counts into 64-bit offsets (one CTA)
+// exclusive scan of the chunk counts into 64-bit offsets (one CTA): warp w
+// owns a contiguous range read in coalesced rows of 32; a pass sums the
+// ranges, one warp scans the sums, and a second pass scans row by row with
+// shuffles on top of the carry
 __global__ void __launch_bounds__(1024) k_w_scan(const uint32_t *counts, uint64_t *offsets, uint64_t m,
                                                  uint64_t *meta, const uint32_t *status)
 {
     if (block_skips(status)) return;
-    __shared__ uint64_t part[1024];
-    const uint64_t per = (m + 1023) / 1024;
-    const uint64_t a = threadIdx.x * per, b = a + per < m ? a + per : m;
+    __shared__ uint64_t wsum[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t per = ((m + 31) / 32 + 31) / 32 * 32;
+    const uint64_t a = warp * per, b = a + per < m ? a + per : m;
     uint64_t s = 0;
-    for (uint64_t i = a; i < b; i++) s += counts[i];
-    part[threadIdx.x] = s;
+    for (uint64_t i = a + lane; i < b; i += 32) s += counts[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) wsum[warp] = s;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const uint64_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (warp == 0) {
+        const uint64_t v = wsum[lane];
+        uint64_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        wsum[lane] = incl - v;
+        if (lane == 31) meta[0] = incl;
     }
-    uint64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-    for (uint64_t i = a; i < b; i++) {
-        offsets[i] = run;
-        run += counts[i];
+    __syncthreads();
+    uint64_t carry = wsum[warp];
+    for (uint64_t r = a; r < b; r += 32) {
+        const uint64_t i = r + lane;
+        const uint32_t c = i < b ? counts[i] : 0u;
+        uint32_t incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (i < b) offsets[i] = carry + incl - c;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (threadIdx.x == 1023) meta[0] = part[1023];
 }
 
 // ordered write: the chunk's pairs at its offset, by ascending u (one warp

@@ -51,6 +51,11 @@ def check_single(f_np, t):
     mt.mt_sync_status(ws)
     assert np.array_equal(W.cpu().numpy().view(np.uint64), W_ref), f"fused triplets {f_np.shape}"
     assert np.array_equal(lab.cpu().numpy().view(np.uint32), lab_ref), f"fused labels {f_np.shape}"
+    pairs.zero_()
+    k2, root2 = mt.mt_build_step(f, W, t, lab, pairs, ws)
+    assert (k2, root2) == (k, root) and np.array_equal(pairs[:k].cpu().numpy().view(np.uint32), p_ref)
+    assert np.array_equal(W.cpu().numpy().view(np.uint64), W_ref), f"step triplets {f_np.shape}"
+    assert np.array_equal(lab.cpu().numpy().view(np.uint32), lab_ref), f"step labels {f_np.shape}"
 
 
 def check_wide(f_np, t):

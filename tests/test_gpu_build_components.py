@@ -1,4 +1,5 @@
-"""mt_build_components against the oracle and the separate calls (bit-exact).
+"""mt_build_components and mt_build_step against the oracle and the separate
+calls (bit-exact).
 
 The call builds the triplets and labels the components of G_t inside the
 repair pass. Its triplets must equal mt_build_triplets_cfg's and the oracle's,
@@ -131,3 +132,73 @@ def test_rejects_nan_and_bad_cfg():
         mt.mt_build_components(f, W, 0.0, lab, ws, eps=float("nan"))
     with pytest.raises(mt.MtError):
         mt.mt_build_components(f, W, 0.0, lab, ws, cfg=mt.MT_CFG_SMALL_TILES)
+
+
+def _step(f_np, t, eps=0.0, flags=0, cfg=0, cap=None):
+    f = torch.from_numpy(np.ascontiguousarray(f_np, dtype=np.float32)).cuda()
+    n = f.numel()
+    W = torch.empty(n, dtype=torch.int64, device="cuda")
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    P = torch.empty((n // 2 + 1 if cap is None else cap, 2), dtype=torch.int32, device="cuda")
+    ws = mt.workspace(mt.grid_of(f))
+    k, root = mt.mt_build_step(f, W, t, lab, P, ws, eps=eps, flags=flags, cfg=cfg, allow_partial=cap is not None)
+    return (W.cpu().numpy().view(np.uint64), lab.cpu().numpy().view(np.uint32),
+            P[:min(k, P.shape[0])].cpu().numpy().view(np.uint32), k, root)
+
+
+@pytest.mark.parametrize("case", ["white", "ties", "grf", "lognorm", "plane", "line"])
+def test_step_equals_oracle(case):
+    """mt_build_step: triplets, labels, pairs (counted in the repair pass)
+    and the root, against the oracle."""
+    f = _field(case)
+    W_ref = oracle.merge_tree(f)
+    p_ref, roots = oracle.pairs(W_ref)
+    for t in (float(np.median(f)), float(np.max(f))):
+        W, lab, P, k, root = _step(f, t)
+        assert np.array_equal(W, W_ref)
+        assert np.array_equal(lab, oracle.components(f, t))
+        assert k == len(p_ref) and root == int(roots[0])
+        assert np.array_equal(P, p_ref)
+
+
+@pytest.mark.parametrize("case", ["ties", "lognorm"])
+def test_step_simplified_equals_oracle(case):
+    f = _field(case)
+    W_ref = oracle.merge_tree(f)
+    p, _ = oracle.pairs(W_ref)
+    eps = float(np.sort(oracle.persistence(f, W_ref, p[:, 0]))[len(p) // 2])
+    t = float(np.quantile(f, 0.6))
+    W, lab, P, k, _ = _step(f, t, eps=eps)
+    ref = oracle.simplified_pairs(f, W_ref, eps)
+    assert k == len(ref) and np.array_equal(P, ref)
+    assert np.array_equal(lab, oracle.simplified_components(f, W_ref, t, eps))
+
+
+def test_step_split_tree_and_capacity():
+    f = _field("grf")
+    W_ref = oracle.merge_tree(-f)
+    p_ref, _ = oracle.pairs(W_ref)
+    t = float(np.median(f))
+    W, lab, P, k, _ = _step(f, t, flags=mt.MT_SUPERLEVEL)
+    assert np.array_equal(W, W_ref) and np.array_equal(P, p_ref)
+    assert np.array_equal(lab, oracle.components(-f, -t))
+    cap = len(p_ref) // 3
+    W, lab, P, k, _ = _step(f, t, flags=mt.MT_SUPERLEVEL, cap=cap)
+    assert k == len(p_ref)  # the true count, with the first cap pairs written
+    assert np.array_equal(P, p_ref[:cap])
+
+
+def test_step_equals_separate_calls_large():
+    g = fields.lognormal((200, 256, 250), seed=6, sigma=0.8, slope=-2.0, device="cuda").contiguous()
+    n = g.numel()
+    ws = mt.workspace(mt.grid_of(g))
+    t = float(torch.quantile(g.reshape(-1)[::97].float(), 0.5))
+    W0, W1 = torch.empty(n, dtype=torch.int64, device="cuda"), torch.empty(n, dtype=torch.int64, device="cuda")
+    L0, L1 = torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.int32, device="cuda")
+    P0, P1 = (torch.empty((n // 2, 2), dtype=torch.int32, device="cuda") for _ in range(2))
+    mt.mt_build_triplets(g, W0, ws)
+    k0, r0 = mt.mt_persistence_pairs(g, W0, P0, ws)
+    mt.mt_components_at(g, W0, t, L0, ws)
+    k1, r1 = mt.mt_build_step(g, W1, t, L1, P1, ws)
+    assert (k0, r0) == (k1, r1)
+    assert torch.equal(W0, W1) and torch.equal(L0, L1) and torch.equal(P0[:k0], P1[:k1])
