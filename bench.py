@@ -131,7 +131,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ algorithmic bytes
-def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 32), fused: bool = True) -> dict:
+def algorithmic_bytes(n: int, shape, npairs: int, tile=(16, 16, 16), fused: bool = True) -> dict:
     """Bytes the method must move per step, by kernel:
       tile    init: read f (4n) + write W (8n); plus two triplet reads per
               merged edge inside the tiles, 16 (E' - C)

@@ -262,8 +262,8 @@ mt_status mt_batch_prepare(const float *d_arena, const mt_grid *h_grids, uint32_
 
 /* Launch configurations (bits of cfg; 0 is the default). Every
  * configuration gives the same results; they differ only in speed:
- *   MT_CFG_SMALL_TILES  16x16x8 tiles of 256 threads instead of 32x16x16 tiles
- *                       of 1024 threads (batches only: small fields leave
+ *   MT_CFG_SMALL_TILES  16x16x8 tiles of 256 threads instead of 16x16x16 tiles
+ *                       of 512 threads (batches only: small fields leave
  *                       most of a large tile empty)
  *   MT_CFG_FOUR_ROUNDS  4 level buckets per tile instead of 8: the in-tile
  *                       edges are merged, and their vertices repaired, in 4

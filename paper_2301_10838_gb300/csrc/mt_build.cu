@@ -584,7 +584,7 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
 // set when every tile lies inside the grid (grid sides multiples of the tile
 // sides), which drops all partial-tile bounds checks.
 template <int LX, int LY, int LZ, int NT, int NB, class Loc, bool FULL, bool WIDE = false>
-__global__ void __launch_bounds__(NT, NT >= 1024 ? 2 : 1536 / NT) k_tile(Loc loc, uint32_t ntiles, uint32_t *queue,
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 2 : NT == 512 ? 4 : 1536 / NT) k_tile(Loc loc, uint32_t ntiles, uint32_t *queue,
                                                                       uint32_t *status)
 {
     if (queue == nullptr) {
@@ -1076,16 +1076,21 @@ __global__ void __launch_bounds__(NT, 3) k_repair(Loc loc, uint32_t *status, con
 
 // ------------------------------------------------------------ host side
 
-// Tile shapes. Variant 0: 32 x 16 x 16, 8192 vertices, about 108 KiB of
-// shared memory, two CTAs of 1024 threads per SM (16^3 tiles with four CTAs
-// of 512 threads measured slower on the 1024^3 field: more cross-tile edges).
-// Variant 1: 16 x 16 x 8, 2048 vertices, about 26 KiB, six CTAs of 256
-// threads per SM, for batches of small fields that would leave most of a
-// large tile empty. 8 level buckets in both.
+// Tile shapes. Variant 0: 16 x 16 x 16, 4096 vertices, about 53 KiB of
+// shared memory, four CTAs of 512 threads per SM (32 x 16 x 16 tiles in two
+// CTAs of 1024 threads run the tile kernel 6 % slower on the 1024^3 field:
+// with four CTAs per SM, one CTA's round barrier leaves three others to
+// issue). Variant 1: 16 x 16 x 8, 2048 vertices, about 26 KiB, six CTAs of
+// 256 threads per SM, for batches of small fields that would leave most of a
+// large tile empty. 8 level buckets in both. Variant 2: 32 x 16 x 16 bricks
+// of 8192 vertices, the unit of the repair pass of a single field (its
+// shared-memory copies of target chains serve twice as many vertices as in
+// a 16^3 brick) and of the wide-id tile kernel.
 constexpr int kBuckets = 8;
 template <int V> struct Variant;
-template <> struct Variant<0> { static constexpr int LX = 5, LY = 4, LZ = 4, NT = 1024; };
+template <> struct Variant<0> { static constexpr int LX = 4, LY = 4, LZ = 4, NT = 512; };
 template <> struct Variant<1> { static constexpr int LX = 4, LY = 4, LZ = 3, NT = 256; };
+template <> struct Variant<2> { static constexpr int LX = 5, LY = 4, LZ = 4, NT = 1024; };
 
 void tile_shape(int variant, uint32_t &tx, uint32_t &ty, uint32_t &tz)
 {
@@ -1206,13 +1211,22 @@ static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, i
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     PhaseScope ps(kRepair, st);
-    if constexpr (std::is_same<Loc, OneField>::value) {  // labels only for a single field
+    if constexpr (std::is_same<Loc, OneField>::value) {
+        // a single field is repaired (and labelled) in 32 x 16 x 16 bricks
+        using RV = Variant<2>;
+        OneField rl = loc;
+        rl.d.ntx = (loc.d.nx + (1u << RV::LX) - 1) >> RV::LX;
+        rl.d.nty = (loc.d.ny + (1u << RV::LY) - 1) >> RV::LY;
+        const uint32_t rn = rl.d.ntx * rl.d.nty * ((loc.d.nz + (1u << RV::LZ) - 1) >> RV::LZ);
         if (la)
-            return (cfg & MT_CFG_REPAIR_256) ? launch_repair<V, 256, Loc, true>(loc, ntiles, status, st, *la)
-                                             : launch_repair<V, 512, Loc, true>(loc, ntiles, status, st, *la);
+            return (cfg & MT_CFG_REPAIR_256) ? launch_repair<2, 256, Loc, true>(rl, rn, status, st, *la)
+                                             : launch_repair<2, 512, Loc, true>(rl, rn, status, st, *la);
+        return (cfg & MT_CFG_REPAIR_256) ? launch_repair<2, 256>(rl, rn, status, st)
+                                         : launch_repair<2, 512>(rl, rn, status, st);
+    } else {
+        return (cfg & MT_CFG_REPAIR_256) ? launch_repair<V, 256>(loc, ntiles, status, st)
+                                         : launch_repair<V, 512>(loc, ntiles, status, st);
     }
-    return (cfg & MT_CFG_REPAIR_256) ? launch_repair<V, 256>(loc, ntiles, status, st)
-                                     : launch_repair<V, 512>(loc, ntiles, status, st);
 }
 
 cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
@@ -1236,11 +1250,12 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
 }
 
 // The tile kernel with 64-bit ids and 128-bit output words (the wide path):
-// one CTA per 32x16x16 tile, no face buffer.
+// one CTA per 32x16x16 tile (the tiles whose boundaries k_w_cross merges),
+// no face buffer.
 cudaError_t launch_tile_wide(const float *f, uint64_t *W2, uint32_t nx, uint32_t ny, uint32_t nz, float sg,
                              uint32_t *status, cudaStream_t st)
 {
-    using VV = Variant<0>;
+    using VV = Variant<2>;
     using TS = Tile<VV::LX, VV::LY, VV::LZ, VV::NT>;
     OneField loc;
     loc.d = FieldDesc{};
@@ -1281,7 +1296,7 @@ cudaError_t launch_batch_build(const FieldDesc *d_descs, uint32_t nfields, uint3
     if (e != cudaSuccess) return e;
     // persistent grid: as many CTAs as fit on the GPU at once
     const bool small = cfg & MT_CFG_SMALL_TILES;
-    const int per_sm = small ? 1536 / Variant<1>::NT : 2;
+    const int per_sm = small ? 1536 / Variant<1>::NT : 2048 / Variant<0>::NT;
     const int grid = device_sms() * per_sm;
     if (small) return run_build<1>(loc, ntiles, queue, grid, false, status, st, cfg);
     return run_build<0>(loc, ntiles, queue, grid, false, status, st, cfg);

@@ -4,7 +4,7 @@ Run by test_gpu_stress_tables.py in a child process: the library is loaded
 from MT_LIBRARY, and every case compares the CUDA path with the oracle bit
 for bit. With the stress build's tables (one probe in the tile kernel's edge
 hash; 16 target slots, 8 chain copies and a 32-entry minima list per
-8192-vertex repair tile; 64 chain starts per label brick) the fields below
+repair tile; 64 chain starts per label brick) the fields below
 overflow every table, so the paths for a full table -- merge in place,
 repair a branch minimum from the overflow bitmap, chase a target or a chain start along
 the global chain -- carry most of the work.
