@@ -274,25 +274,55 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
         kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
     }
 
-    // 2. seed: T[l] = (l, first vertex of the closed in-tile neighbourhood);
-    //    key histogram for the level buckets
+    // Spare bits of a triplet (ids take IDB of each 16-bit half) carry a
+    // mask of neighbour directions d (-x, -y, -z, +x, +y, +z): from the seed
+    // to step 4 the lower neighbours of the vertex, from step 4 on (inner
+    // vertices only) its cross mask: the lower neighbours that descend to
+    // another minimum. Only those edges can join two components; the scan of
+    // the vertex's level bucket reads them from here. The bucket repair of
+    // the vertex rewrites its triplet and so clears the bits; minima never
+    // carry any (a minimum has no lower neighbour).
+    auto tid_s = [](uint32_t w) { return (w >> 16) & IDM; };
+    auto tid_v = [](uint32_t w) { return w & IDM; };
+    auto xmask = [](uint32_t w) { return ((w >> IDB) & 7u) | (((w >> (16 + IDB)) & 7u) << 3); };
+    auto with_mask = [](uint32_t w, uint32_t m) { return w | ((m & 7u) << IDB) | ((m >> 3) << (16 + IDB)); };
+    constexpr uint32_t SPARE = ~(IDM | (IDM << 16));
+    auto nbr = [](uint32_t l, uint32_t d) -> uint32_t {
+        const uint32_t a = d < 3 ? d : d - 3;
+        const uint32_t step = 1u << (a == 0 ? 0 : a == 1 ? LX : LX + LY);
+        return d < 3 ? l - step : l + step;
+    };
+
+    // 2. seed: T[l] = (l, first vertex of the closed in-tile neighbourhood)
+    //    with l's lower neighbours in the spare bits; key histogram for the
+    //    level buckets
     const uint32_t kmin_t = kmin, kmax_t = kmax;
     const float bscale = (float)BINS / ((float)(kmax_t - kmin_t) + 1.0f);
     auto bin_of = [&](uint32_t k) { return min((uint32_t)BINS - 1, (uint32_t)((float)(k - kmin_t) * bscale)); };
     for (uint32_t l = threadIdx.x; l < TV; l += NT) {
         if (!valid(l)) continue;
         const uint32_t lx = lxo(l), ly = lyo(l), lz = lzo(l);
-        uint32_t b = l, kb = K[l];
+        const uint32_t kl = K[l];
+        uint32_t b = l, kb = kl;
         atomicAdd(&hist[bin_of(kb)], 1u);
         // candidates in ascending local index order: an earlier id wins ties,
-        // so an earlier candidate replaces b only if strictly lower
-        if (lz > 0 && K[l - TX * TY] <= kb) b = l - TX * TY, kb = K[b];
-        if (ly > 0 && K[l - TX] <= kb && (K[l - TX] < kb || l - TX < b)) b = l - TX, kb = K[b];
-        if (lx > 0 && K[l - 1] <= kb && (K[l - 1] < kb || l - 1 < b)) b = l - 1, kb = K[b];
-        if (lx + 1 < wx && K[l + 1] < kb) b = l + 1, kb = K[b];
-        if (ly + 1 < wy && K[l + TX] < kb) b = l + TX, kb = K[b];
-        if (lz + 1 < wz && K[l + TX * TY] < kb) b = l + TX * TY, kb = K[b];
-        T[l] = sm_pack(l, b);
+        // so an earlier candidate replaces b only if strictly lower; a
+        // neighbour is lower than l if its key is lower, or equal and its id
+        // earlier (the -x, -y, -z neighbours)
+        const uint32_t kmz = lz > 0 ? K[l - TX * TY] : 0xFFFFFFFFu, kmy = ly > 0 ? K[l - TX] : 0xFFFFFFFFu,
+                       kmx = lx > 0 ? K[l - 1] : 0xFFFFFFFFu;
+        const uint32_t kpx = lx + 1 < wx ? K[l + 1] : 0u, kpy = ly + 1 < wy ? K[l + TX] : 0u,
+                       kpz = lz + 1 < wz ? K[l + TX * TY] : 0u;
+        if (lz > 0 && kmz <= kb) b = l - TX * TY, kb = kmz;
+        if (ly > 0 && kmy <= kb && (kmy < kb || l - TX < b)) b = l - TX, kb = kmy;
+        if (lx > 0 && kmx <= kb && (kmx < kb || l - 1 < b)) b = l - 1, kb = kmx;
+        if (lx + 1 < wx && kpx < kb) b = l + 1, kb = kpx;
+        if (ly + 1 < wy && kpy < kb) b = l + TX, kb = kpy;
+        if (lz + 1 < wz && kpz < kb) b = l + TX * TY, kb = kpz;
+        const uint32_t lm = (uint32_t)(lx > 0 && kmx <= kl) | (uint32_t)(ly > 0 && kmy <= kl) << 1 |
+                            (uint32_t)(lz > 0 && kmz <= kl) << 2 | (uint32_t)(lx + 1 < wx && kpx < kl) << 3 |
+                            (uint32_t)(ly + 1 < wy && kpy < kl) << 4 | (uint32_t)(lz + 1 < wz && kpz < kl) << 5;
+        T[l] = with_mask(sm_pack(l, b), lm);
     }
     __syncthreads();
 
@@ -305,17 +335,17 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
         for (uint32_t l = threadIdx.x; l < TV; l += NT) {
             if (!valid(l)) continue;
             const uint32_t w = vT[l];
-            if (sm_v(w) == l) {
+            if (tid_v(w) == l) {
                 SC[l] = (uint16_t)l;
                 continue;
             }
-            uint32_t x = sm_v(w);
+            uint32_t x = tid_v(w);
             for (uint32_t h = 0; h < (uint32_t)TV; h++) {
                 const uint32_t wx_ = vT[x];
-                if (sm_v(wx_) == x) break;
-                x = sm_v(wx_);
+                if (tid_v(wx_) == x) break;
+                x = tid_v(wx_);
             }
-            if (x != sm_v(w)) vT[l] = sm_pack(l, x);
+            if (x != tid_v(w)) vT[l] = sm_pack(l, x) | (w & SPARE);
         }
         const uint32_t c = threadIdx.x < (uint32_t)BINS ? hist[threadIdx.x] : 0u;
         uint32_t incl = c;
@@ -347,20 +377,8 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
         }
         s_thr[threadIdx.x] = lo;
     }
-    // Spare bits of an inner vertex's triplet (ids take IDB of each 16-bit
-    // half) carry its cross mask: bit d is set when its neighbour in direction
-    // d (-x, -y, -z, +x, +y, +z) is lower and descends to another minimum.
-    // Only those edges can join two components; the scan of the vertex's
-    // level bucket reads them from here. The bucket repair of the vertex
-    // rewrites its triplet and so clears the bits; minima never carry any.
-    auto tid_s = [](uint32_t w) { return (w >> 16) & IDM; };
-    auto tid_v = [](uint32_t w) { return w & IDM; };
-    auto xmask = [](uint32_t w) { return ((w >> IDB) & 7u) | (((w >> (16 + IDB)) & 7u) << 3); };
-    auto nbr = [](uint32_t l, uint32_t d) -> uint32_t {
-        const uint32_t a = d < 3 ? d : d - 3;
-        const uint32_t step = 1u << (a == 0 ? 0 : a == 1 ? LX : LX + LY);
-        return d < 3 ? l - step : l + step;
-    };
+    // The cross masks of step 4 (from there on, until the bucket repair
+    // rewrites the triplet) are kept in the same bits.
 
     // 4. cross masks, then a counting sort of the vertices by segment:
     //    inner vertices by level bucket (segments 0 .. NB-1), minima last
@@ -369,26 +387,21 @@ __device__ __forceinline__ void tile_body(const FieldDesc &fd, uint32_t tile, ui
     for (uint32_t l = threadIdx.x; l < TV; l += NT) {
         if (!valid(l)) continue;
         const uint32_t w0 = vT[l];
-        const uint32_t dl = sm_v(w0);
+        const uint32_t dl = tid_v(w0);
         if (dl == l) {  // a minimum
             atomicAdd(&s_bcur[NB], 1u);
             continue;
         }
-        const uint32_t lx = lxo(l), ly = lyo(l), lz = lzo(l), kl = K[l];
+        const uint32_t lm = xmask(w0);  // lower neighbours, from the seed
         uint32_t m = 0;
 #pragma unroll
         for (uint32_t d = 0; d < 6; d++) {
-            const bool in = d == 0 ? lx > 0 : d == 1 ? ly > 0 : d == 2 ? lz > 0 :
-                            d == 3 ? lx + 1 < wx : d == 4 ? ly + 1 < wy : lz + 1 < wz;
-            if (!in) continue;
+            if (!((lm >> d) & 1u)) continue;
             const uint32_t w = nbr(l, d);
-            if (!kbefore(K[w], w, kl, l)) continue;
-            const uint32_t Tw = vT[w];
-            const uint32_t dw = tid_v(Tw) == w ? w : tid_v(Tw);  // w's minimum
-            if (dw != dl) m |= 1u << d;
+            if (tid_v(vT[w]) != dl) m |= 1u << d;  // w's minimum is another
         }
-        atomicAdd(&s_bcur[bucket_of(kl)], 1u);
-        vT[l] = sm_pack(l, dl) | ((m & 7u) << IDB) | ((m >> 3) << (16 + IDB));
+        atomicAdd(&s_bcur[bucket_of(K[l])], 1u);
+        vT[l] = with_mask(sm_pack(l, dl), m);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
