@@ -345,6 +345,18 @@ def run_ours(args):
     achieved = ab[dom] / (tot / calls / 1e3) / 1e9
     prof = traffic_record(dom) if side == 1024 else {}
     traffic = prof.get("dram_bytes_per_launch")
+    # the same kernel against the issue rate: warp instructions per launch
+    # (ncu, same record) over the live time, against 4 warp schedulers per SM
+    # each issuing one instruction per cycle at the SM clock measured under load
+    winst = prof.get("warp_instructions_per_launch")
+    issue = None
+    if winst and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_i = sms * 4 * clk["sm_mhz"] * 1e6
+        got_i = winst / (tot / calls / 1e3)
+        issue = {"warp_instructions_per_launch": winst, "achieved_ginst_s": round(got_i / 1e9, 1),
+                 "peak_ginst_s": round(peak_i / 1e9, 1), "frac": round(got_i / peak_i, 4),
+                 "peak_from": f"{sms} SMs x 4 schedulers x {clk['sm_mhz']:.0f} MHz"}
     step_bytes = sum(ab[k] for k in ("tile", "merge", "repair", "pairs", "labels"))
 
     # end to end through the public API with pinned host buffers: every step
@@ -484,7 +496,7 @@ def run_ours(args):
                          # profile shows: the model bytes above are not what bounds this kernel
                          "dram_gbs": round(traffic / (tot / calls / 1e3) / 1e9, 1) if traffic else None,
                          "dram_frac": round(traffic / (tot / calls / 1e3) / 1e9 / peak, 4) if traffic else None,
-                         "limiter": prof.get("limiter"), "profile": prof.get("from")},
+                         "limiter": prof.get("limiter"), "profile": prof.get("from"), "issue": issue},
             "step_roofline": {"algorithmic_bytes": step_bytes,
                               "frac": round(step_bytes / (ms_step / 1e3) / 1e9 / peak, 4)},
             "phases_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in phases.items()},
