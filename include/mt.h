@@ -101,16 +101,17 @@ mt_status mt_build_triplets_ex(const float *d_f, mt_grid g, uint64_t *d_W, void 
                                void *stream);
 
 /* mt_build_triplets_ex with a launch configuration cfg (MT_CFG_FOUR_ROUNDS,
- * MT_CFG_REPAIR_256; MT_CFG_SMALL_TILES is for batches and gives
- * MT_ERR_INVALID). The triplets do not depend on cfg. */
+ * MT_CFG_REPAIR_256, MT_CFG_LARGE_TILES; MT_CFG_SMALL_TILES is for batches
+ * and gives MT_ERR_INVALID, as does any other bit). The triplets do not
+ * depend on cfg. */
 mt_status mt_build_triplets_cfg(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
                                 uint32_t cfg, void *stream);
 
 /* Autotuner for single fields: builds the tree of d_f once per
- * configuration (cfg 0, 2, 4, 6: the single-field knobs) to warm up and three
- * times timed (CUDA events on `stream`), writes the best times to ms[0..3]
- * (in that order) and the fastest configuration to *best. d_W receives the
- * triplets. Synchronises. */
+ * configuration (cfg 0, 2, 4, 6, 8, 10, 12, 14: the single-field knobs) to
+ * warm up and three times timed (CUDA events on `stream`), writes the best
+ * times to ms[0..7] (in that order; ms holds 8 floats) and the fastest
+ * configuration to *best. d_W receives the triplets. Synchronises. */
 mt_status mt_build_autotune(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
                             void *stream, float *ms, uint32_t *best);
 
@@ -270,11 +271,20 @@ mt_status mt_batch_prepare(const float *d_arena, const mt_grid *h_grids, uint32_
  *                       rounds by level instead of 8 (Algorithm 1 merges the
  *                       edges in any order)
  *   MT_CFG_REPAIR_256   the repair kernel (Algorithm 5) in CTAs of 256
- *                       threads instead of 512 */
+ *                       threads instead of 512
+ *   MT_CFG_LARGE_TILES  32x16x16 tiles of 1024 threads, two CTAs per SM,
+ *                       instead of 16x16x16 tiles of 512 threads, four per SM
+ *                       (single fields only: fewer edges between tiles
+ *                       against fewer warps per SM to issue while a tile
+ *                       waits at a round barrier)
+ * A batch takes the configurations 0 .. MT_CFG_COUNT - 1; a single field the
+ * even ones of 0 .. 15 (MT_CFG_SINGLE_MASK). */
 #define MT_CFG_SMALL_TILES 1u
 #define MT_CFG_FOUR_ROUNDS 2u
 #define MT_CFG_REPAIR_256 4u
+#define MT_CFG_LARGE_TILES 8u
 #define MT_CFG_COUNT 8
+#define MT_CFG_SINGLE_MASK (MT_CFG_FOUR_ROUNDS | MT_CFG_REPAIR_256 | MT_CFG_LARGE_TILES)
 
 /* Enqueues the batched build and pair compaction on `stream`: memsets and
  * kernel launches only, nothing synchronises, so it may be captured in a

@@ -42,7 +42,9 @@ __all__ = [
     "MT_CFG_SMALL_TILES",
     "MT_CFG_FOUR_ROUNDS",
     "MT_CFG_REPAIR_256",
+    "MT_CFG_LARGE_TILES",
     "MT_CFG_COUNT",
+    "MT_CFG_SINGLE_MASK",
     "mt_components_at_ex",
     "mt_persistence_pairs_noalloc",
     "mt_wide_workspace_bytes",
@@ -82,7 +84,9 @@ MT_SUPERLEVEL = 1  # flag of the _ex calls: the tree of -f (superlevel sets, the
 MT_CFG_SMALL_TILES = 1  # 16x16x8 tiles of 256 threads (batches only)
 MT_CFG_FOUR_ROUNDS = 2  # 4 level buckets (merge/repair rounds) per tile instead of 8
 MT_CFG_REPAIR_256 = 4   # repair CTAs of 256 threads instead of 512
-MT_CFG_COUNT = 8
+MT_CFG_LARGE_TILES = 8  # 32x16x16 tiles of 1024 threads (single fields only)
+MT_CFG_COUNT = 8        # batch configurations 0 .. 7
+MT_CFG_SINGLE_MASK = MT_CFG_FOUR_ROUNDS | MT_CFG_REPAIR_256 | MT_CFG_LARGE_TILES
 STATUS_NAMES = {0: "MT_OK", -1: "MT_ERR_INVALID", -2: "MT_ERR_TOO_LARGE", -3: "MT_ERR_NONFINITE",
                 -4: "MT_ERR_CAPACITY", -5: "MT_ERR_CUDA", -6: "MT_ERR_NOMEM", -7: "MT_ERR_TIMEOUT",
                 -8: "MT_ERR_BUSY"}
@@ -281,7 +285,8 @@ def mt_build_triplets_ex(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, fla
 def mt_build_triplets_cfg(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, flags: int, cfg: int,
                           stream=None) -> None:
     """mt_build_triplets_ex with a launch configuration (MT_CFG_FOUR_ROUNDS,
-    MT_CFG_REPAIR_256 bits); the triplets do not depend on it."""
+    MT_CFG_REPAIR_256, MT_CFG_LARGE_TILES bits); the triplets do not depend
+    on it."""
     g = grid_of(f)
     n = f.numel()
     _check(load().mt_build_triplets_cfg(_dev(f, "f", (torch.float32,)), g, _dev(W, "W", _I64, n),
@@ -290,16 +295,16 @@ def mt_build_triplets_cfg(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, fl
 
 
 def mt_build_autotune(f: torch.Tensor, W: torch.Tensor, ws: torch.Tensor, flags: int = 0, stream=None):
-    """Times the single-field configurations (cfg 0, 2, 4, 6); returns
+    """Times the single-field configurations (cfg 0, 2, .., 14); returns
     ({cfg: best ms}, best cfg). W receives the triplets."""
     g = grid_of(f)
     n = f.numel()
-    ms = (ctypes.c_float * 4)()
+    ms = (ctypes.c_float * 8)()
     best = ctypes.c_uint32(0)
     _check(load().mt_build_autotune(_dev(f, "f", (torch.float32,)), g, _dev(W, "W", _I64, n),
                                     _dev(ws, "ws", (torch.uint8,)), ws.numel(), int(flags), _stream_ptr(stream),
                                     ctypes.cast(ms, ctypes.c_void_p), ctypes.byref(best)), "mt_build_autotune")
-    return {c: float(ms[i]) for i, c in enumerate((0, 2, 4, 6))}, int(best.value)
+    return {2 * i: float(ms[i]) for i in range(8)}, int(best.value)
 
 
 def mt_build_components(f: torch.Tensor, W: torch.Tensor, t: float, labels: torch.Tensor, ws: torch.Tensor,

@@ -17,7 +17,8 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 //   [0, 256)     status word, round flag
 //   [256, 512)   meta: npairs, number of roots, root
 //   [512, ...)   per-chunk counts of the ordered compaction
-//   then, for a build, the face buffers (face_words(0) u32 per tile)
+//   then, for a build, the face buffers (face_words(v) u32 per tile of the
+//   tile shape v in use: 16^3, or 32x16x16 with MT_CFG_LARGE_TILES)
 size_t workspace_bytes(uint64_t n)
 {
     const uint64_t nchunks = (n + kCompactChunk - 1) / kCompactChunk;
@@ -27,7 +28,8 @@ size_t workspace_bytes(uint64_t n)
 size_t build_workspace_bytes(uint32_t nx, uint32_t ny, uint32_t nz)
 {
     const uint64_t n = (uint64_t)nx * ny * nz;
-    return workspace_bytes(n) + align256(tile_count(0, nx, ny, nz) * face_words(0) * sizeof(uint32_t));
+    const uint64_t f0 = tile_count(0, nx, ny, nz) * face_words(0), f2 = tile_count(2, nx, ny, nz) * face_words(2);
+    return workspace_bytes(n) + align256((f0 > f2 ? f0 : f2) * sizeof(uint32_t));
 }
 
 uint32_t *build_faces(void *base, uint64_t n)
@@ -150,7 +152,7 @@ mt_status mt_build_triplets_ex(const float *d_f, mt_grid g, uint64_t *d_W, void 
 mt_status mt_build_triplets_cfg(const float *d_f, mt_grid g, uint64_t *d_W, void *d_ws, size_t ws_bytes, uint32_t flags,
                                 uint32_t cfg, void *stream)
 {
-    if (cfg >= MT_CFG_COUNT || (cfg & MT_CFG_SMALL_TILES)) return MT_ERR_INVALID;
+    if (cfg & ~MT_CFG_SINGLE_MASK) return MT_ERR_INVALID;
     uint64_t n;
     mt_status st = grid_n(g, n);
     if (st != MT_OK) return st;
@@ -170,7 +172,7 @@ mt_status mt_build_triplets_cfg(const float *d_f, mt_grid g, uint64_t *d_W, void
 mt_status mt_build_components(const float *d_f, mt_grid g, uint64_t *d_W, float t, float eps, uint32_t flags,
                               uint32_t cfg, uint32_t *d_labels, void *d_ws, size_t ws_bytes, void *stream)
 {
-    if (cfg >= MT_CFG_COUNT || (cfg & MT_CFG_SMALL_TILES)) return MT_ERR_INVALID;
+    if (cfg & ~MT_CFG_SINGLE_MASK) return MT_ERR_INVALID;
     uint64_t n;
     mt_status st = grid_n(g, n);
     if (st != MT_OK) return st;
@@ -193,7 +195,7 @@ mt_status mt_build_step(const float *d_f, mt_grid g, uint64_t *d_W, float t, flo
                         uint32_t *d_labels, uint32_t *d_pairs, uint64_t cap, uint64_t *h_npairs, uint32_t *h_root,
                         void *d_ws, size_t ws_bytes, void *stream)
 {
-    if (cfg >= MT_CFG_COUNT || (cfg & MT_CFG_SMALL_TILES)) return MT_ERR_INVALID;
+    if (cfg & ~MT_CFG_SINGLE_MASK) return MT_ERR_INVALID;
     uint64_t n;
     mt_status st = grid_n(g, n);
     if (st != MT_OK) return st;
@@ -232,14 +234,15 @@ mt_status mt_build_autotune(const float *d_f, mt_grid g, uint64_t *d_W, void *d_
         cudaEventDestroy(a);
         return MT_ERR_CUDA;
     }
-    static const uint32_t cfgs[4] = {0u, MT_CFG_FOUR_ROUNDS, MT_CFG_REPAIR_256, MT_CFG_FOUR_ROUNDS | MT_CFG_REPAIR_256};
+    constexpr int kCfgs = 8;  // the even configurations 0 .. 14
     mt_status st = MT_OK;
-    for (int i = 0; i < 4 && st == MT_OK; i++) {
-        st = mt_build_triplets_cfg(d_f, g, d_W, d_ws, ws_bytes, flags, cfgs[i], stream);  // warm-up
+    for (int i = 0; i < kCfgs && st == MT_OK; i++) {
+        const uint32_t cfg = 2u * (uint32_t)i;
+        st = mt_build_triplets_cfg(d_f, g, d_W, d_ws, ws_bytes, flags, cfg, stream);  // warm-up
         float best_ms = 1e30f;
         for (int rep = 0; rep < 3 && st == MT_OK; rep++) {
             cudaEventRecord(a, s);
-            st = mt_build_triplets_cfg(d_f, g, d_W, d_ws, ws_bytes, flags, cfgs[i], stream);
+            st = mt_build_triplets_cfg(d_f, g, d_W, d_ws, ws_bytes, flags, cfg, stream);
             cudaEventRecord(b, s);
             if (cudaEventSynchronize(b) != cudaSuccess) st = MT_ERR_CUDA;
             float t = 0.f;
@@ -252,9 +255,9 @@ mt_status mt_build_autotune(const float *d_f, mt_grid g, uint64_t *d_W, void *d_
     cudaEventDestroy(b);
     if (st != MT_OK) return st;
     int k = 0;
-    for (int i = 1; i < 4; i++)
+    for (int i = 1; i < kCfgs; i++)
         if (ms[i] < ms[k]) k = i;
-    *best = cfgs[k];
+    *best = 2u * (uint32_t)k;
     return mt_sync_status(d_ws, stream);
 }
 

@@ -1109,6 +1109,8 @@ void tile_shape(int variant, uint32_t &tx, uint32_t &ty, uint32_t &tz)
 {
     if (variant == 1) {
         tx = 1u << Variant<1>::LX, ty = 1u << Variant<1>::LY, tz = 1u << Variant<1>::LZ;
+    } else if (variant == 2) {
+        tx = 1u << Variant<2>::LX, ty = 1u << Variant<2>::LY, tz = 1u << Variant<2>::LZ;
     } else {
         tx = 1u << Variant<0>::LX, ty = 1u << Variant<0>::LY, tz = 1u << Variant<0>::LZ;
     }
@@ -1242,10 +1244,12 @@ static cudaError_t run_build(const Loc &loc, uint32_t ntiles, uint32_t *queue, i
     }
 }
 
-cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
-                         uint32_t *faces, float sg, cudaStream_t st, uint32_t cfg, const LabelArgs *la)
+// A single field in the tile shape of variant V (0, or 2 with MT_CFG_LARGE_TILES).
+template <int V>
+static cudaError_t build_one(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
+                             uint32_t *faces, float sg, cudaStream_t st, uint32_t cfg, const LabelArgs *la)
 {
-    using VV = Variant<0>;
+    using VV = Variant<V>;
     OneField loc;
     loc.d = FieldDesc{};
     loc.d.f = f;
@@ -1259,7 +1263,14 @@ cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, 
     const uint32_t ntz = (nz + (1u << VV::LZ) - 1) >> VV::LZ;
     const uint64_t ntiles = (uint64_t)loc.d.ntx * loc.d.nty * ntz;
     const bool full = nx % (1u << VV::LX) == 0 && ny % (1u << VV::LY) == 0 && nz % (1u << VV::LZ) == 0;
-    return run_build<0>(loc, (uint32_t)ntiles, nullptr, 0, full, ws.status, st, cfg, la);
+    return run_build<V>(loc, (uint32_t)ntiles, nullptr, 0, full, ws.status, st, cfg, la);
+}
+
+cudaError_t launch_build(const float *f, uint64_t *W, uint32_t nx, uint32_t ny, uint32_t nz, Workspace &ws,
+                         uint32_t *faces, float sg, cudaStream_t st, uint32_t cfg, const LabelArgs *la)
+{
+    if (cfg & MT_CFG_LARGE_TILES) return build_one<2>(f, W, nx, ny, nz, ws, faces, sg, st, cfg, la);
+    return build_one<0>(f, W, nx, ny, nz, ws, faces, sg, st, cfg, la);
 }
 
 // The tile kernel with 64-bit ids and 128-bit output words (the wide path):

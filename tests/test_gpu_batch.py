@@ -119,7 +119,7 @@ def test_batch_512_config_equals_oracle(tmp_path, monkeypatch):
 
 def test_single_field_configurations_equal_oracle(tmp_path, monkeypatch):
     """mt_build_triplets_cfg: every single-field configuration (level buckets,
-    repair CTA size) gives the oracle's triplets, on a full-tile grid and on
+    repair CTA size, tile shape) gives the oracle's triplets, on a full-tile grid and on
     ragged ones; the single-field tuner picks one and caches it."""
     monkeypatch.setenv("MT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     from paper_2301_10838_gb300 import autotune
@@ -132,13 +132,13 @@ def test_single_field_configurations_equal_oracle(tmp_path, monkeypatch):
         f = torch.from_numpy(f_np).cuda()
         W = torch.empty(f.numel(), dtype=torch.int64, device="cuda")
         ws = mt.workspace(mt.grid_of(f))
-        for cfg in (0, mt.MT_CFG_FOUR_ROUNDS, mt.MT_CFG_REPAIR_256, mt.MT_CFG_FOUR_ROUNDS | mt.MT_CFG_REPAIR_256):
+        for cfg in range(0, mt.MT_CFG_SINGLE_MASK + 1, 2):
             W.zero_()
             mt.mt_build_triplets_cfg(f, W, ws, 0, cfg)
             mt.mt_sync_status(ws)
             assert np.array_equal(W.cpu().numpy().view(np.uint64), W_ref), (shape, cfg)
         cfg, ms = autotune.tune_single(f, W, ws)
-        assert cfg in ms and len(ms) == 4
+        assert cfg in ms and len(ms) == 8
         assert autotune.tune_single(f, W, ws) == (cfg, None)  # from the cache
     with pytest.raises(mt.MtError):
         mt.mt_build_triplets_cfg(f, W, ws, 0, mt.MT_CFG_SMALL_TILES)

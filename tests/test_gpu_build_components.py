@@ -91,7 +91,7 @@ def test_split_tree_labels_equal_oracle():
         assert np.array_equal(lab, oracle.components(-f, -t)), q
 
 
-@pytest.mark.parametrize("cfg", [0, 2, 4, 6])
+@pytest.mark.parametrize("cfg", [0, 2, 4, 6, 8, 10, 12, 14])
 def test_every_configuration(cfg):
     f = _field("lognorm")
     t = float(np.median(f))
