@@ -222,17 +222,24 @@ __global__ void __launch_bounds__(256) k_w_cross(FieldW f, Geo g, uint32_t ntx, 
 // Representative (Algorithm 4) at level S: hop while the link's saddle is at
 // or below S in the order; return the vertex where the walk stops. Concurrent
 // repairs only move a word's target further along its own chain below the
-// same saddle, so either half may be old or new.
+// same saddle, so either half may be old or new. The next word is read
+// beside the saddle's value, before the test that decides whether it is
+// needed (the target of a link is a vertex of the grid, so the read stays in
+// bounds); the same in the climbs of the merges, whose reads repeat until
+// both halves carry one tag, measured slower.
 __device__ __forceinline__ uint64_t w_rep(const uint64_t *W, const FieldW &f, uint64_t x, uint64_t S, float fS,
                                           uint32_t &steps)
 {
+    uint64_t lo, hi;
+    ld_word(W, x, lo, hi);
     for (;;) {
-        uint64_t lo, hi;
-        ld_word(W, x, lo, hi);
         const uint64_t s = lo & kIdMask, v = hi & kIdMask;
         if (s == x && v == x) return x;
-        if (s != S && !before_w(f[s], s, fS, S)) return x;
-        x = v;
+        const float fs = f[s];
+        uint64_t nlo, nhi;
+        ld_word(W, v, nlo, nhi);
+        if (s != S && !before_w(fs, s, fS, S)) return x;
+        x = v, lo = nlo, hi = nhi;
         if (++steps > kChaseLimit) return x;
     }
 }
