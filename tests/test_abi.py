@@ -119,6 +119,35 @@ def test_simplification_and_branch_argument_errors_need_no_gpu(lib):
                                        None) == -2
 
 
+def test_launch_configurations_need_no_gpu(lib):
+    """A single field takes the even configurations 0 .. 14 (level buckets,
+    repair CTA size, tile shape); the batch-only small-tile bit and unknown
+    bits are rejected before any device work, and the workspace holds the
+    face buffers of both tile shapes a single field can use."""
+    P = ctypes.c_void_p(256)
+    for cfg in (mt.MT_CFG_SMALL_TILES, 16, 0x80000000, mt.MT_CFG_SMALL_TILES | mt.MT_CFG_LARGE_TILES):
+        g = mt.Grid(4, 4, 4)
+        nbytes = lib.mt_workspace_bytes(g)
+        assert lib.mt_build_triplets_cfg(P, g, P, P, nbytes, 0, cfg, None) == -1, cfg
+    assert mt.MT_CFG_SINGLE_MASK == mt.MT_CFG_FOUR_ROUNDS | mt.MT_CFG_REPAIR_256 | mt.MT_CFG_LARGE_TILES
+    assert not mt.MT_CFG_SINGLE_MASK & mt.MT_CFG_SMALL_TILES
+
+    def faces(shape, tile):
+        nt = 1
+        for a, b in zip(shape, tile):
+            nt *= -(-a // b)
+        tx, ty, tz = tile
+        return nt * 2 * (ty * tz + tx * tz + tx * ty) * 4  # u32 per tile: both sides of three faces
+
+    for shape in ((1024, 1024, 1024), (33, 16, 16), (17, 17, 17), (40, 3, 300), (1, 1, 1)):
+        nx, ny, nz = shape
+        n = nx * ny * nz
+        chunks = -(-n // 4096)
+        need = 512 + max(faces(shape, (16, 16, 16)), faces(shape, (32, 16, 16)))
+        got = lib.mt_workspace_bytes(mt.Grid(nx, ny, nz))
+        assert got >= need + 4 * chunks, (shape, got, need)
+
+
 def test_library_is_sm103a_only():
     """The build passes exactly one -gencode, for sm_103a."""
     assert mtbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
