@@ -6,8 +6,9 @@ file (``MT_AUTOTUNE_CACHE``, default ``~/.cache/mt_gb300_autotune.json``)
 keyed by the GPU name and a shape class, so that later runs on the same kind
 of input skip the timing. Every configuration gives the same results.
 
-Configurations are the MT_CFG_* bits of include/mt.h: tile shape (batches),
-level buckets per tile (the merge/repair rounds) and the repair CTA size.
+Configurations are the MT_CFG_* bits of include/mt.h: tile shape (batches:
+16x16x8 or 16x16x16; single fields: 16x16x16 or 32x16x16), level buckets per
+tile (the merge/repair rounds) and the repair CTA size.
 """
 
 from __future__ import annotations
