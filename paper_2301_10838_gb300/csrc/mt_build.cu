@@ -1135,14 +1135,15 @@ static cudaError_t tile_attrs()
 {
     using VV = Variant<V>;
     using TS = Tile<VV::LX, VV::LY, VV::LZ, VV::NT>;
-    static bool done = false;  // per instantiation
-    if (done) return cudaSuccess;
+    static AttrFlags flags;  // per instantiation
+    int dev;
+    if (!flags.pending(dev)) return cudaSuccess;
     auto ktile = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, NB, Loc, FULL>;
     cudaError_t e = cudaFuncSetAttribute(ktile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS::kSmem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(ktile, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    done = true;
+    flags.done(dev);
     return cudaSuccess;
 }
 
@@ -1151,12 +1152,13 @@ static cudaError_t repair_attrs()
 {
     using VV = Variant<V>;
     using RS = RepairShape<VV::LX, VV::LY, VV::LZ>;
-    static bool done = false;  // per instantiation
-    if (done) return cudaSuccess;
+    static AttrFlags flags;  // per instantiation
+    int dev;
+    if (!flags.pending(dev)) return cudaSuccess;
     const cudaError_t e = cudaFuncSetAttribute(k_repair<VV::LX, VV::LY, VV::LZ, NT, Loc, LAB>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)(LAB ? RS::kSmemLab : RS::kSmem));
-    if (e == cudaSuccess) done = true;
+    if (e == cudaSuccess) flags.done(dev);
     return e;
 }
 
@@ -1295,17 +1297,18 @@ cudaError_t launch_tile_wide(const float *f, uint64_t *W2, uint32_t nx, uint32_t
     const uint64_t ntiles = (uint64_t)loc.d.ntx * loc.d.nty * ntz;
     if (ntiles >= 0x80000000ull) return cudaErrorInvalidValue;
     const bool full = nx % (1u << VV::LX) == 0 && ny % (1u << VV::LY) == 0 && nz % (1u << VV::LZ) == 0;
-    static bool attr[2] = {false, false};
+    static AttrFlags attr[2];
     auto kfull = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, OneField, true, true>;
     auto kpart = k_tile<VV::LX, VV::LY, VV::LZ, VV::NT, kBuckets, OneField, false, true>;
     auto kern = full ? kfull : kpart;
-    if (!attr[full]) {
+    int dev;
+    if (attr[full].pending(dev)) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS::kSmem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        attr[full] = true;
+        attr[full].done(dev);
     }
     kern<<<(unsigned)ntiles, VV::NT, TS::kSmem, st>>>(loc, (uint32_t)ntiles, nullptr, status);
     count_launch();

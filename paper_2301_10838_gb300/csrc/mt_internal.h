@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
@@ -74,6 +75,28 @@ uint32_t *build_faces(void *base, uint64_t n);
 uint32_t face_words(int variant);
 uint64_t tile_count(int variant, uint32_t nx, uint32_t ny, uint32_t nz);
 int device_sms();
+// A kernel's function attributes (its dynamic shared-memory size, the
+// carveout) belong to the context of one device, so a process that uses
+// several GPUs sets them on each. One AttrFlags per kernel: pending() is true
+// while the current device has not had them set (and always for device
+// ordinals past the table), done() records that it has.
+struct AttrFlags {
+    static constexpr int kDevices = 64;
+    std::atomic<bool> set[kDevices];
+    bool pending(int &dev)
+    {
+        dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) {
+            dev = -1;
+            return true;
+        }
+        return !set[dev].load(std::memory_order_relaxed);
+    }
+    void done(int dev)
+    {
+        if (dev >= 0) set[dev].store(true, std::memory_order_relaxed);
+    }
+};
 // Reads meta[0..2] (if meta is given) and the status word into out[0..3]
 // through mapped pinned memory (mt_api.cu); synchronises st.
 cudaError_t readback(const uint64_t *meta, const uint32_t *status, cudaStream_t st, uint64_t out[4]);

@@ -408,12 +408,13 @@ cudaError_t launch_labels(const float *f, const uint64_t *W, uint32_t nx, uint32
     PhaseScope ps(kLabels, st);
     count_launch();
     const uint32_t ntx = (nx + 31) >> kLabLX, nty = (ny + 15) >> kLabLY, ntz = (nz + 15) >> kLabLZ;
-    static bool attr = false;
-    if (!attr) {
+    static AttrFlags attr;
+    int dev;
+    if (attr.pending(dev)) {
         const cudaError_t e =
             cudaFuncSetAttribute(k_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLabSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.done(dev);
     }
     k_labels<<<ntx * nty * ntz, kLabThreads, kLabSmem, st>>>(Field{f, sg}, W, nx, ny, nz, ntx, nty, t, eps,
                                                             labels, ws.status);
